@@ -1,0 +1,195 @@
+/*
+ * lddmm.h -- C interface of the GB300 library for band-limited Jacobi
+ * PDE-EPDiff LDDMM subject to the state equation, solved by inexact
+ * Gauss-Newton-Krylov (Hernandez, arXiv:1807.11560, Sections 2.5, 2.7, 3.1, 3.2).
+ *
+ * Problem (Section 3.2, Eqs. 50-52): minimise over the band-limited initial
+ * velocity v0
+ *     E(v0) = 1/2 <L~ v0, v0>_{l2} + sigma^-2 || m(1) - I1 ||^2_{L2}
+ * subject to BL EPDiff  d_t v + ad~^dagger_v v = 0 (Eq. 51) and the state
+ * equation d_t m + grad m . iota(v) = 0 on the image grid (Eq. 52), m(0) = I0,
+ * with L = (Id - alpha Lap)^s (Eq. 1).
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions shared by every call
+ * ---------------------------------------------------------------------------
+ * Domain      the periodic unit box [0,1)^d, d = 2 or 3; grid N_1 x .. x N_d,
+ *             spacing h_j = 1/N_j; <f,g>_{L2} = h^d sum_x f g.
+ * Images      real, C order [N_1][N_2]([N_3]), axis 0 slowest.
+ * BL fields   complex interleaved (re, im), layout [d][K_1][K_2]([K_3]),
+ *             band index q_j in FFT order with signed frequency
+ *             f = q (q < K/2) or q - K.  The Nyquist slot q_j = K_j/2 is held
+ *             at zero; a field is the Hermitian array of a real vector field.
+ *             Inputs are symmetrised on entry ((a(k) + conj a(-k))/2, Nyquist
+ *             slots dropped), which is what the real field iota(a) depends on
+ *             (Eq. 46).  Outputs are Hermitian with zero Nyquist slots.
+ * iota/pi     iota(a)(x) = sum_k a(k) exp(2 pi i k.x) (Eq. 46);
+ *             pi(f)(k) = N^-d sum_x f(x) exp(-2 pi i k.x) on the band.
+ * L~, K~      symbols (1 + 4 pi^2 alpha |k|^2)^s and its inverse.
+ * <.,.>_V     Re sum_k Lhat(k) conj(a(k)) b(k)  (Eq. 47).
+ * Precision   LDDMM_FP32: float images and complex64 BL fields, FP32
+ *             arithmetic with FP64 reductions; LDDMM_FP64: double and
+ *             complex128 throughout.  Every pointer argument has the element
+ *             type of the context's precision.
+ * Pointers    any pointer argument may be a device pointer or a host pointer
+ *             (pageable or pinned); host data are staged through the
+ *             context's device buffers with cudaMemcpyAsync on the context
+ *             stream.  The caller owns every pointer it passes; the library
+ *             never keeps one after the call returns.
+ * Ordering    work is issued on the context stream (opts.stream, default the
+ *             legacy default stream); every call returns after that stream
+ *             has finished the call's work, so outputs are ready on return.
+ * Errors      every call returns an lddmm_status; nothing aborts or throws
+ *             across this interface.  On failure lddmm_last_error() holds a
+ *             one-line message.  A CUDA error leaves the context unusable
+ *             except for lddmm_destroy.
+ * Threads     a context is used by one host thread at a time.
+ * Discretisation (the paper states continuous equations only):
+ *             Nt uniform Heun steps for the BL sweeps; semi-Lagrangian
+ *             RK2-characteristic transport with trilinear periodic
+ *             interpolation on the image grid; central differences for
+ *             grad m; products of BL fields formed on a padded grid of
+ *             ceil(3K/2) points per axis (exact truncated convolution).
+ */
+#ifndef LDDMM_H
+#define LDDMM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lddmm_ctx lddmm_ctx;
+
+typedef enum {
+  LDDMM_OK = 0,
+  LDDMM_EINVAL = 1,      /* bad argument (sizes, null pointer, unknown option) */
+  LDDMM_ENOMEM = 2,      /* device allocation failed */
+  LDDMM_ECUDA = 3,       /* a CUDA call failed; see lddmm_last_error */
+  LDDMM_ESTATE = 4,      /* call out of order (e.g. hessvec before gradient) */
+  LDDMM_ENONFINITE = 5,  /* energy or gradient became NaN/Inf */
+  LDDMM_ETIMEOUT = 6,    /* reserved: a bounded device wait gave up */
+  LDDMM_ENOTCONV = 7     /* reserved for callers; gn_solve reports line-search
+                            failure in lddmm_report.ls_failed instead */
+} lddmm_status;
+
+typedef enum { LDDMM_FP64 = 0, LDDMM_FP32 = 1 } lddmm_precision;
+
+typedef struct {
+  int precision;        /* lddmm_precision; default LDDMM_FP32 */
+  void* stream;         /* cudaStream_t; NULL = legacy default stream */
+  double pcg_tol;       /* PCG stops when ||r||_V <= pcg_tol ||b||_V; default 1e-12 */
+  double armijo_c;      /* Armijo constant; default 1e-4 */
+  int max_halvings;     /* line-search halvings of eps = 1; default 10 */
+  int use_graphs;       /* replay the Hessian-vector product from a CUDA graph; default 1 */
+} lddmm_opts;
+
+/* Report of lddmm_gn_solve.  The per-iteration arrays are optional
+ * caller-owned host arrays of length n_gn (NULL to skip). */
+typedef struct {
+  int gn_iters;          /* Gauss-Newton iterations completed */
+  int pcg_iters;         /* total PCG iterations (Hessian-vector products) */
+  int ls_failed;         /* 1 if the last line search accepted no step */
+  double E_initial;      /* E at the starting v0 */
+  double E_final;        /* E at the returned v0 */
+  double gnorm_initial;  /* ||g||_V at the starting v0 */
+  double gnorm_final;    /* ||g||_V at the last gradient evaluation */
+  double* E_hist;        /* optional: E before each GN iteration */
+  double* eps_hist;      /* optional: accepted step length of each iteration */
+  int* pcg_hist;         /* optional: PCG iterations of each iteration */
+} lddmm_report;
+
+/* Defaults for lddmm_opts (precision FP32, legacy stream, tol 1e-12,
+ * c = 1e-4, 10 halvings, graphs on). */
+void lddmm_default_opts(lddmm_opts* opts);
+
+/* Create a registration context (Section 3.2).
+ *   ndim    2 or 3.
+ *   grid    ndim image sizes N_j >= 2 (int array, host).
+ *   K       ndim band sizes: even, 2 <= K_j <= N_j (int array, host).
+ *   alpha   > 0, s >= 1: L = (Id - alpha Lap)^s (Eq. 1).
+ *   sigma   > 0: data weight 1/sigma^2 (Eq. 50).
+ *   Nt      >= 1 time steps on [0,1].
+ *   opts    NULL for defaults.
+ * Allocates every device buffer the context needs (histories for Nt steps,
+ * padded-grid caches, transform scratch).  Returns LDDMM_ENOMEM if the
+ * device lacks memory, LDDMM_EINVAL for bad sizes.  *out is NULL on failure. */
+int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K,
+                 double alpha, int s, double sigma, int Nt, const lddmm_opts* opts);
+
+/* Copy the source I0 and target I1 images (Section 2.1) into the context.
+ * Invalidates any linearisation point. */
+int lddmm_set_images(lddmm_ctx* ctx, const void* I0, const void* I1);
+
+/* E(v0) of Eq. 50 (shoot, transport, FP64 reductions).  Does not disturb the
+ * linearisation point left by lddmm_gradient. */
+int lddmm_energy(lddmm_ctx* ctx, const void* v0, double* E_out);
+
+/* V-gradient g = v0 + W(0) (Eqs. 53-55): forward shoot and transport, the
+ * terminal U(1) = K~ pi(lambda(1) grad m(1)), lambda(1) = -2/sigma^2 (m(1)-I1),
+ * and the backward reduced adjoint Jacobi sweep.  Writes g (BL field) and,
+ * if E_out is not NULL, E(v0).  Sets the linearisation point for hessvec. */
+int lddmm_gradient(lddmm_ctx* ctx, const void* v0, void* g_out, double* E_out);
+
+/* Gauss-Newton Hessian-vector product in V at the last gradient point
+ * (Eqs. 30-31 and 56-58 with every adjoint-weighted term dropped, Section 2.7):
+ * incremental BL EPDiff from dv, incremental state transport on the grid,
+ * dU(1) = K~ pi(-2/sigma^2 dm(1) grad m(1)), backward adjoint Jacobi sweep;
+ * Hdv = dv + dW(0).  LDDMM_ESTATE if no gradient was computed since the
+ * last set_images. */
+int lddmm_hessvec(lddmm_ctx* ctx, const void* dv, void* Hdv_out);
+
+/* Inexact Gauss-Newton-Krylov (Eqs. 44-45): for each of n_gn iterations,
+ * gradient, n_pcg iterations of CG in the V inner product on H p = -g
+ * (early stop on ||r||_V <= pcg_tol ||b||_V or non-positive curvature),
+ * Armijo backtracking v0 <- v0 + eps p.  v0_inout is read and overwritten.
+ * rep may be NULL.  Stops early, with rep->ls_failed = 1, when a line search
+ * accepts no step. */
+int lddmm_gn_solve(lddmm_ctx* ctx, void* v0_inout, int n_gn, int n_pcg, lddmm_report* rep);
+
+/* ---------------------------------------------------------------------------
+ * Component calls: single steps of the hot path, exposed for testing and for
+ * callers composing their own solvers.  Same conventions as above.
+ * ------------------------------------------------------------------------- */
+
+/* iota (Eq. 46): ncomp band-limited scalar fields [ncomp][K..] -> grid
+ * values [ncomp][N..] on the image grid. */
+int lddmm_iota(lddmm_ctx* ctx, const void* a, int ncomp, void* f_out);
+
+/* pi: ncomp grid fields [ncomp][N..] -> band coefficients [ncomp][K..]. */
+int lddmm_pi(lddmm_ctx* ctx, const void* f, int ncomp, void* a_out);
+
+/* ad~^dagger_v u = K~ pi[(Dv)^T L~u + D(L~u) v + L~u div v] (Eq. 48), products
+ * on the padded grid. */
+int lddmm_ad_dagger(lddmm_ctx* ctx, const void* v, const void* u, void* out);
+
+/* ad~_v w = pi[Dv w - Dw v] (Eq. 49). */
+int lddmm_ad(lddmm_ctx* ctx, const void* v, const void* w, void* out);
+
+/* Heun shoot of BL EPDiff (Eq. 51) from v0; writes v(1).  Uses its own
+ * buffers: the linearisation point is kept. */
+int lddmm_shoot(lddmm_ctx* ctx, const void* v0, void* v1_out);
+
+/* Shoot and transport I0 (Eqs. 51-52); writes m(1) on the image grid.  Keeps
+ * the linearisation point. */
+int lddmm_transport(lddmm_ctx* ctx, const void* v0, void* m1_out);
+
+/* dm(1) of the last lddmm_hessvec call (incremental state, Eq. 31). */
+int lddmm_last_dm1(lddmm_ctx* ctx, void* dm1_out);
+
+/* Number of CUDA kernels this context has launched since creation (graph
+ * replays count each kernel node). */
+long long lddmm_kernel_count(const lddmm_ctx* ctx);
+
+/* One-line description of the last error on this context (never NULL). */
+const char* lddmm_last_error(const lddmm_ctx* ctx);
+
+/* Free every device buffer of the context.  NULL is allowed. */
+void lddmm_destroy(lddmm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDDMM_H */

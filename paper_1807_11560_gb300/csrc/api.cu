@@ -1,0 +1,987 @@
+// Host side of the GB300 LDDMM library: the C interface of include/lddmm.h.
+//
+// A context owns, per problem, every device buffer of the method:
+//   * twiddle tables of the image-grid plan (N) and of the padded product
+//     plan (M = ceil(3K/2)), and the symbol table L^(k);
+//   * two trajectories ("lin", the Gauss-Newton linearisation point, and
+//     "trial", used by energy evaluations and component calls), each with the
+//     BL history v_n, the Heun predictors v*_{n+1}, the 24 padded-grid fields
+//     (v, Dv, L v, D(L v)) of every Heun stage point, the grid velocities
+//     iota(v_n), the state history m_n and the characteristic displacements;
+//   * the tangent history dv_n and its grid velocities, two ping-pong pairs
+//     for dm and s = grad m . dv, the transform scratch and BL temporaries.
+// The time loops run on the host and enqueue kernels on one stream; the
+// Hessian-vector product can be captured once per linearisation point into a
+// CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <initializer_list>
+#include <utility>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lddmm.h"
+#include "internal.h"
+
+struct lddmm_ctx {
+  int precision;
+  void* impl;
+  std::string err;
+};
+
+namespace lddmm {
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279;
+
+struct Fail {
+  int code;
+};
+
+template <typename T>
+struct State {
+  cplx<T>* vh = nullptr;    // [Nt+1][3][Kvol]
+  cplx<T>* vsh = nullptr;   // [Nt][3][Kvol]
+  T* cache = nullptr;       // [2 Nt][24][Mvol]
+  T* vgrid = nullptr;       // [Nt+1][3][Nvol]
+  T* mh = nullptr;          // [Nt+1][Nvol]
+  T* off = nullptr;         // [Nt][3][Nvol]
+};
+
+template <typename T>
+struct Impl {
+  using C = cplx<T>;
+  std::string* err = nullptr;
+  int ndim = 3, duser = 3;
+  Dims N{}, M{};
+  Band K{};
+  int Nt = 1, s = 2;
+  double alpha = 0, sigma = 1, dt = 1;
+  long long Nvol = 0, Mvol = 0, Kvol = 0;
+  lddmm_opts opts{};
+  cudaStream_t st = nullptr;
+  Plan<T> full{}, pad{};
+  T* Lhat = nullptr;
+  T *I0 = nullptr, *I1 = nullptr;
+  State<T> lin, trial;
+  bool have_images = false, have_lin = false, have_dm1 = false;
+  C *T1 = nullptr, *T2 = nullptr;
+  T *X = nullptr, *P = nullptr;
+  C *k1 = nullptr, *aU = nullptr, *aW = nullptr, *Ut = nullptr, *Wt = nullptr, *U = nullptr,
+    *W = nullptr, *dstar = nullptr, *vin = nullptr, *vout = nullptr, *gbuf = nullptr;
+  C *px = nullptr, *pr = nullptr, *pd = nullptr, *pq = nullptr, *vsol = nullptr, *vtry = nullptr;
+  C* dvh = nullptr;          // [Nt+1][3][Kvol]
+  T* dvgrid = nullptr;       // [Nt+1][3][Nvol]
+  T *dm[2] = {nullptr, nullptr}, *sb[2] = {nullptr, nullptr};
+  T* fterm = nullptr;        // [3][Nvol]
+  double *partial = nullptr, *dres = nullptr;
+  double* hres = nullptr;    // pinned host mirror of dres
+  long long launches = 0;
+  std::vector<void*> allocs;
+  // graph of one Hessian-vector product (input dvh[0], output vout)
+  cudaGraphExec_t hv_exec = nullptr;
+  long long hv_nodes = 0;
+  cudaStream_t cap = nullptr;
+  cudaEvent_t ev = nullptr;
+
+  // ---------------------------------------------------------------- utils
+  void cuda(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+      *err = std::string(what) + ": " + cudaGetErrorString(e);
+      throw Fail{LDDMM_ECUDA};
+    }
+  }
+  void check_launch(const char* what) { cuda(cudaGetLastError(), what); }
+  template <typename P_>
+  void alloc(P_*& p, size_t count) {
+    void* q = nullptr;
+    const size_t bytes = count * sizeof(P_);
+    cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *err = "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e);
+      throw Fail{LDDMM_ENOMEM};
+    }
+    allocs.push_back(q);
+    p = static_cast<P_*>(q);
+  }
+  void release() {
+    if (hv_exec) cudaGraphExecDestroy(hv_exec);
+    hv_exec = nullptr;
+    if (cap) cudaStreamDestroy(cap);
+    cap = nullptr;
+    if (ev) cudaEventDestroy(ev);
+    ev = nullptr;
+    for (void* q : allocs) cudaFree(q);
+    allocs.clear();
+    if (hres) cudaFreeHost(hres);
+    hres = nullptr;
+  }
+
+  static C tw(long long p, int G, int sign, double w = 1.0) {
+    const long long r = ((p % G) + G) % G;
+    const double a = 2.0 * kPi * (double)r / (double)G;
+    return C{(T)(w * std::cos(a)), (T)(w * sign * std::sin(a))};
+  }
+  static int sfreq(int q, int Kq) { return (2 * q < Kq) ? q : q - Kq; }
+
+  void make_plan(Plan<T>& p, Dims g) {
+    p.g = g;
+    p.b = K;
+    const int H1 = K.h1;
+    std::vector<C> e3f((size_t)K.k3 * g.n3), e2f((size_t)K.k2 * g.n2), e1f((size_t)H1 * g.n1),
+        e1b((size_t)g.n1 * H1), e2b((size_t)g.n2 * K.k2), e3b((size_t)g.n3 * K.k3);
+    for (int k = 0; k < K.k3; ++k)
+      for (int x = 0; x < g.n3; ++x) {
+        e3f[(size_t)k * g.n3 + x] = tw((long long)sfreq(k, K.k3) * x, g.n3, +1);
+        e3b[(size_t)x * K.k3 + k] = tw((long long)sfreq(k, K.k3) * x, g.n3, -1);
+      }
+    for (int k = 0; k < K.k2; ++k)
+      for (int x = 0; x < g.n2; ++x) {
+        e2f[(size_t)k * g.n2 + x] = tw((long long)sfreq(k, K.k2) * x, g.n2, +1);
+        e2b[(size_t)x * K.k2 + k] = tw((long long)sfreq(k, K.k2) * x, g.n2, -1);
+      }
+    for (int h = 0; h < H1; ++h)
+      for (int x = 0; x < g.n1; ++x) {
+        e1f[(size_t)h * g.n1 + x] = tw((long long)h * x, g.n1, +1, h == 0 ? 1.0 : 2.0);
+        e1b[(size_t)x * H1 + h] = tw((long long)h * x, g.n1, -1);
+      }
+    auto up = [&](C*& dst, std::vector<C>& src) {
+      alloc(dst, src.size());
+      cuda(cudaMemcpy(dst, src.data(), src.size() * sizeof(C), cudaMemcpyHostToDevice), "twiddles");
+    };
+    up(p.E3f, e3f);
+    up(p.E2f, e2f);
+    up(p.E1f, e1f);
+    up(p.E1b, e1b);
+    up(p.E2b, e2b);
+    up(p.E3b, e3b);
+  }
+
+  void make_state(State<T>& S) {
+    alloc(S.vh, (size_t)(Nt + 1) * 3 * Kvol);
+    alloc(S.vsh, (size_t)Nt * 3 * Kvol);
+    alloc(S.cache, (size_t)2 * Nt * 24 * Mvol);
+    alloc(S.vgrid, (size_t)(Nt + 1) * 3 * Nvol);
+    alloc(S.mh, (size_t)(Nt + 1) * Nvol);
+    alloc(S.off, (size_t)Nt * 3 * Nvol);
+  }
+
+  void create(int nd, const int* grid, const int* band, double a, int s_, double sg, int nt,
+              const lddmm_opts& o) {
+    ndim = nd;
+    duser = nd;
+    N = Dims{grid[0], grid[1], nd == 3 ? grid[2] : 1};
+    K.k1 = band[0];
+    K.k2 = band[1];
+    K.k3 = nd == 3 ? band[2] : 1;
+    K.h1 = K.k1 / 2;
+    auto padn = [](int k) { return k == 1 ? 1 : (3 * k + 1) / 2; };
+    M = Dims{padn(K.k1), padn(K.k2), padn(K.k3)};
+    Nt = nt;
+    s = s_;
+    alpha = a;
+    sigma = sg;
+    dt = 1.0 / nt;
+    Nvol = N.vol();
+    Mvol = M.vol();
+    Kvol = K.vol();
+    opts = o;
+    st = (cudaStream_t)o.stream;
+    cuda(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "stream");
+    cuda(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+
+    make_plan(full, N);
+    make_plan(pad, M);
+    std::vector<T> L((size_t)Kvol);
+    for (int q1 = 0; q1 < K.k1; ++q1)
+      for (int q2 = 0; q2 < K.k2; ++q2)
+        for (int q3 = 0; q3 < K.k3; ++q3) {
+          const double f1 = sfreq(q1, K.k1), f2 = sfreq(q2, K.k2), f3 = sfreq(q3, K.k3);
+          L[((size_t)q1 * K.k2 + q2) * K.k3 + q3] =
+              (T)std::pow(1.0 + 4.0 * kPi * kPi * alpha * (f1 * f1 + f2 * f2 + f3 * f3), (double)s);
+        }
+    alloc(Lhat, (size_t)Kvol);
+    cuda(cudaMemcpy(Lhat, L.data(), L.size() * sizeof(T), cudaMemcpyHostToDevice), "Lhat");
+
+    alloc(I0, (size_t)Nvol);
+    alloc(I1, (size_t)Nvol);
+    make_state(lin);
+    make_state(trial);
+    const long long H1 = K.h1;
+    const long long t1 = std::max(33LL * H1 * K.k2 * N.n3, 24LL * H1 * K.k2 * M.n3);
+    const long long t2 = std::max(33LL * H1 * N.n2 * N.n3, 24LL * H1 * M.n2 * M.n3);
+    alloc(T1, (size_t)t1);
+    alloc(T2, (size_t)t2);
+    alloc(X, (size_t)24 * Mvol);
+    alloc(P, (size_t)9 * Mvol);
+    for (C** b : {&k1, &aU, &aW, &Ut, &Wt, &U, &W, &dstar, &vin, &vout, &gbuf, &px, &pr, &pd, &pq,
+                  &vsol, &vtry})
+      alloc(*b, (size_t)3 * Kvol);
+    alloc(dvh, (size_t)(Nt + 1) * 3 * Kvol);
+    alloc(dvgrid, (size_t)(Nt + 1) * 3 * Nvol);
+    for (int i = 0; i < 2; ++i) {
+      alloc(dm[i], (size_t)Nvol);
+      alloc(sb[i], (size_t)Nvol);
+    }
+    alloc(fterm, (size_t)3 * Nvol);
+    alloc(partial, (size_t)kReduceBlocks);
+    alloc(dres, 8);
+    cuda(cudaMallocHost(&hres, 8 * sizeof(double)), "cudaMallocHost");
+    cuda(cudaDeviceSynchronize(), "create");
+  }
+
+  // ------------------------------------------------------------ staging
+  // user BL vector (duser comps) -> hermitian 3-comp device vector
+  void load_bl(const void* user, C* dst) {
+    cuda(cudaMemcpyAsync(vin, user, (size_t)duser * Kvol * sizeof(C), cudaMemcpyDefault, st),
+         "copy BL input");
+    if (duser < 3)
+      cuda(cudaMemsetAsync(vin + (size_t)duser * Kvol, 0, (size_t)(3 - duser) * Kvol * sizeof(C), st),
+           "memset");
+    hermitianize<T>(vin, dst, 3, K, st);
+    ++launches;
+    check_launch("hermitianize");
+  }
+  void store_bl(const C* src, void* user) {
+    cuda(cudaMemcpyAsync(user, src, (size_t)duser * Kvol * sizeof(C), cudaMemcpyDefault, st),
+         "copy BL output");
+  }
+  void sync(const char* what) { cuda(cudaStreamSynchronize(st), what); }
+
+  // -------------------------------------------------------- descriptors
+  IotaDesc<T> block24(const C* srcA, const C* srcB, T* dst) const {
+    IotaDesc<T> d{};
+    d.nf = 24;
+    for (int c = 0; c < 3; ++c) {
+      d.src[c] = srcA + c * Kvol;
+      d.deriv[c] = -1;
+      d.applyL[c] = 0;
+      d.src[12 + c] = srcB + c * Kvol;
+      d.deriv[12 + c] = -1;
+      d.applyL[12 + c] = 1;
+      for (int j = 0; j < 3; ++j) {
+        d.src[3 + 3 * c + j] = srcA + c * Kvol;
+        d.deriv[3 + 3 * c + j] = (signed char)j;
+        d.applyL[3 + 3 * c + j] = 0;
+        d.src[15 + 3 * c + j] = srcB + c * Kvol;
+        d.deriv[15 + 3 * c + j] = (signed char)j;
+        d.applyL[15 + 3 * c + j] = 1;
+      }
+    }
+    for (int f = 0; f < 24; ++f) d.dst[f] = dst + f * Mvol;
+    return d;
+  }
+  static PiEpi<T> epi(int ncomp, int nper) {
+    PiEpi<T> e;
+    std::memset(&e, 0, sizeof(e));
+    e.ncomp = ncomp;
+    e.nper = nper;
+    return e;
+  }
+  static void add_out(PiEpi<T>& e, C* dst, int r, double cR,
+                      std::initializer_list<std::pair<const C*, double>> xs) {
+    const int j = e.nout++;
+    e.dst[j] = dst;
+    e.r[j] = r;
+    e.cR[j] = (T)cR;
+    e.nx[j] = 0;
+    for (auto& x : xs) {
+      e.X[j][e.nx[j]] = x.first;
+      e.cX[j][e.nx[j]] = (T)x.second;
+      ++e.nx[j];
+    }
+  }
+
+  // one evaluation of a bracket expression at a Heun stage point
+  void eval(PwMode mode, T* slot, const C* srcA, const C* srcB, const PiEpi<T>& e) {
+    T* dst = (mode == PW_F) ? slot : X;
+    iota_batch<T>(pad, block24(srcA, srcB, dst), Lhat, T1, T2, st);
+    pointwise<T>(mode, X, slot, P, Mvol, st);
+    PiSrc<T> ps{};
+    ps.nf = (mode == PW_GT) ? 9 : 3;
+    for (int f = 0; f < ps.nf; ++f) ps.src[f] = P + f * Mvol;
+    pi_batch<T>(pad, ps, e, Lhat, T1, T2, st);
+    launches += kIotaLaunches + 1 + kPiLaunches;
+    check_launch("bracket evaluation");
+  }
+
+  // iota of `count` BL vectors (3 comps each) onto the image grid
+  void to_grid(const C* hist, int count, T* grid) {
+    for (int v0 = 0; v0 < count; v0 += 11) {
+      const int nv = std::min(11, count - v0);
+      IotaDesc<T> d{};
+      d.nf = 3 * nv;
+      for (int v = 0; v < nv; ++v)
+        for (int c = 0; c < 3; ++c) {
+          const int f = 3 * v + c;
+          d.src[f] = hist + ((long long)(v0 + v) * 3 + c) * Kvol;
+          d.dst[f] = grid + ((long long)(v0 + v) * 3 + c) * Nvol;
+          d.deriv[f] = -1;
+          d.applyL[f] = 0;
+        }
+      iota_batch<T>(full, d, Lhat, T1, T2, st);
+      launches += kIotaLaunches;
+    }
+    check_launch("iota to image grid");
+  }
+
+  // K~ pi of a 3-component image-grid field -> band vector out
+  void project_K(const T* f3, C* out) {
+    PiSrc<T> ps{};
+    ps.nf = 3;
+    for (int c = 0; c < 3; ++c) ps.src[c] = f3 + c * Nvol;
+    PiEpi<T> e = epi(3, 1);
+    e.grp[0] = 0;
+    e.coef[0] = (T)(1.0 / (double)Nvol);
+    e.applyK[0] = 1;
+    add_out(e, out, 0, 1.0, {});
+    pi_batch<T>(full, ps, e, Lhat, T1, T2, st);
+    launches += kPiLaunches;
+    check_launch("projection");
+  }
+
+  // ------------------------------------------------------------- sweeps
+  T* slot(State<T>& S, int k) { return S.cache + (long long)k * 24 * Mvol; }
+  C* vec(C* base, int n) { return base + (long long)n * 3 * Kvol; }
+
+  // Heun shoot of BL EPDiff (Eq. 51); S.vh[0] must hold v0
+  void shoot(State<T>& S) {
+    const double m = 1.0 / (double)Mvol;
+    for (int n = 0; n < Nt; ++n) {
+      C* vn = vec(S.vh, n);
+      C* vs = vec(S.vsh, n);
+      C* vn1 = vec(S.vh, n + 1);
+      PiEpi<T> e1 = epi(3, 1);
+      e1.grp[0] = 0;
+      e1.coef[0] = (T)(-m);
+      e1.applyK[0] = 1;
+      add_out(e1, k1, 0, 1.0, {});
+      add_out(e1, vs, 0, dt, {{vn, 1.0}});
+      eval(PW_F, slot(S, 2 * n), vn, vn, e1);
+      PiEpi<T> e2 = epi(3, 1);
+      e2.grp[0] = 0;
+      e2.coef[0] = (T)(-m);
+      e2.applyK[0] = 1;
+      add_out(e2, vn1, 0, 0.5 * dt, {{vn, 1.0}, {k1, 0.5 * dt}});
+      eval(PW_F, slot(S, 2 * n + 1), vs, vs, e2);
+    }
+  }
+
+  // grid velocities and semi-Lagrangian transport of I0 (Eq. 52)
+  void transport(State<T>& S) {
+    to_grid(S.vh, Nt + 1, S.vgrid);
+    cuda(cudaMemcpyAsync(S.mh, I0, (size_t)Nvol * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy I0");
+    for (int n = 0; n < Nt; ++n)
+      transport_step<T>(S.mh + n * Nvol, S.vgrid + (long long)(n + 1) * 3 * Nvol,
+                        S.vgrid + (long long)n * 3 * Nvol, S.mh + (n + 1) * Nvol,
+                        S.off + (long long)n * 3 * Nvol, N, dt, st);
+    launches += Nt;
+    check_launch("transport");
+  }
+
+  void forward(State<T>& S) {
+    shoot(S);
+    transport(S);
+  }
+
+  // energy pieces into dres[0] (<v0,v0>_V) and dres[1] (sum (m1 - I1)^2)
+  void energy_terms(State<T>& S) {
+    inner_V<T>(S.vh, S.vh, Lhat, 3, Kvol, partial, dres, st);
+    sum_sq_diff<T>(S.mh + (long long)Nt * Nvol, I1, Nvol, partial, dres + 1, st);
+    launches += 4;
+    check_launch("energy reductions");
+  }
+  double read_energy() {
+    cuda(cudaMemcpyAsync(hres, dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "read E");
+    sync("energy");
+    return 0.5 * hres[0] + hres[1] / (sigma * sigma * (double)Nvol);
+  }
+  double dot_V(const C* a, const C* b) {
+    inner_V<T>(a, b, Lhat, 3, Kvol, partial, dres + 2, st);
+    launches += 2;
+    cuda(cudaMemcpyAsync(hres + 2, dres + 2, sizeof(double), cudaMemcpyDeviceToHost, st), "read dot");
+    sync("inner product");
+    return hres[2];
+  }
+
+  // backward reduced adjoint Jacobi sweep (Eqs. 53-54) from (U, W) = (U, 0);
+  // leaves W(0) in W
+  void backward(State<T>& S) {
+    const double m = 1.0 / (double)Mvol;
+    cuda(cudaMemsetAsync(W, 0, (size_t)3 * Kvol * sizeof(C), st), "memset W");
+    for (int n = Nt - 1; n >= 0; --n) {
+      PiEpi<T> e1 = epi(3, 3);
+      e1.grp[0] = 0; e1.coef[0] = (T)m;  e1.applyK[0] = 1;   // ad^dag_v U
+      e1.grp[1] = 1; e1.coef[1] = (T)m;  e1.applyK[1] = 1;   // ad^dag_W v
+      e1.grp[2] = 1; e1.coef[2] = (T)-m; e1.applyK[2] = 0;   // -ad_v W
+      add_out(e1, aU, 0, 1.0, {});
+      add_out(e1, aW, 1, 1.0, {{U, 1.0}});
+      add_out(e1, Ut, 0, dt, {{U, 1.0}});
+      add_out(e1, Wt, 1, dt, {{W, 1.0}, {U, dt}});
+      eval(PW_GT, slot(S, 2 * n + 1), W, U, e1);
+      PiEpi<T> e2 = epi(3, 3);
+      e2.grp[0] = 0; e2.coef[0] = (T)m;  e2.applyK[0] = 1;
+      e2.grp[1] = 1; e2.coef[1] = (T)m;  e2.applyK[1] = 1;
+      e2.grp[2] = 1; e2.coef[2] = (T)-m; e2.applyK[2] = 0;
+      add_out(e2, U, 0, 0.5 * dt, {{U, 1.0}, {aU, 0.5 * dt}});
+      add_out(e2, W, 1, 0.5 * dt, {{W, 1.0}, {aW, 0.5 * dt}, {Ut, 0.5 * dt}});
+      eval(PW_GT, slot(S, 2 * n), Wt, Ut, e2);
+    }
+  }
+
+  // incremental EPDiff (Eq. 30) from dvh[0], exact tangent of the Heun shoot
+  void tangent(State<T>& S) {
+    const double m = 1.0 / (double)Mvol;
+    for (int n = 0; n < Nt; ++n) {
+      C* dn = vec(dvh, n);
+      C* dn1 = vec(dvh, n + 1);
+      PiEpi<T> e1 = epi(3, 1);
+      e1.grp[0] = 0;
+      e1.coef[0] = (T)(-m);
+      e1.applyK[0] = 1;
+      add_out(e1, k1, 0, 1.0, {});
+      add_out(e1, dstar, 0, dt, {{dn, 1.0}});
+      eval(PW_T, slot(S, 2 * n), dn, dn, e1);
+      PiEpi<T> e2 = epi(3, 1);
+      e2.grp[0] = 0;
+      e2.coef[0] = (T)(-m);
+      e2.applyK[0] = 1;
+      add_out(e2, dn1, 0, 0.5 * dt, {{dn, 1.0}, {k1, 0.5 * dt}});
+      eval(PW_T, slot(S, 2 * n + 1), dstar, dstar, e2);
+    }
+  }
+
+  // enqueue one GN Hessian-vector product: input dvh[0], output vout
+  void enqueue_hessvec() {
+    State<T>& S = lin;
+    tangent(S);
+    to_grid(dvh, Nt + 1, dvgrid);
+    grad_dot<T>(S.mh, dvgrid, sb[0], N, st);
+    ++launches;
+    for (int n = 0; n < Nt; ++n) {
+      inc_step<T>(n == 0 ? nullptr : dm[n & 1], sb[n & 1], S.mh + (long long)(n + 1) * Nvol,
+                  dvgrid + (long long)(n + 1) * 3 * Nvol, S.off + (long long)n * 3 * Nvol,
+                  dm[(n + 1) & 1], sb[(n + 1) & 1], N, dt, st);
+    }
+    launches += Nt;
+    terminal_field<T>(S.mh + (long long)Nt * Nvol, dm[Nt & 1], 0, -2.0 / (sigma * sigma), fterm, N, st);
+    ++launches;
+    project_K(fterm, U);
+    backward(S);
+    axpby<T>(vout, 1.0, dvh, 1.0, W, 3 * Kvol, st);
+    ++launches;
+    check_launch("hessvec");
+  }
+
+  // ------------------------------------------------------- public calls
+  void need_images() {
+    if (!have_images) {
+      *err = "images not set (call lddmm_set_images first)";
+      throw Fail{LDDMM_ESTATE};
+    }
+  }
+
+  void set_images(const void* a, const void* b) {
+    cuda(cudaMemcpyAsync(I0, a, (size_t)Nvol * sizeof(T), cudaMemcpyDefault, st), "copy I0");
+    cuda(cudaMemcpyAsync(I1, b, (size_t)Nvol * sizeof(T), cudaMemcpyDefault, st), "copy I1");
+    sync("set_images");
+    have_images = true;
+    have_lin = false;
+    have_dm1 = false;
+  }
+
+  double energy_dev(const C* v0dev) {
+    cuda(cudaMemcpyAsync(trial.vh, v0dev, (size_t)3 * Kvol * sizeof(C), cudaMemcpyDeviceToDevice, st),
+         "copy v0");
+    forward(trial);
+    energy_terms(trial);
+    return read_energy();
+  }
+
+  double energy(const void* v0) {
+    need_images();
+    load_bl(v0, vtry);
+    return energy_dev(vtry);
+  }
+
+  // gradient at the device vector v0dev (hermitian, 3 comps); g -> gdev
+  double gradient_dev(const C* v0dev, C* gdev) {
+    need_images();
+    cuda(cudaMemcpyAsync(lin.vh, v0dev, (size_t)3 * Kvol * sizeof(C), cudaMemcpyDeviceToDevice, st),
+         "copy v0");
+    forward(lin);
+    energy_terms(lin);
+    terminal_field<T>(lin.mh + (long long)Nt * Nvol, I1, 1, -2.0 / (sigma * sigma), fterm, N, st);
+    ++launches;
+    project_K(fterm, U);
+    backward(lin);
+    axpby<T>(gdev, 1.0, lin.vh, 1.0, W, 3 * Kvol, st);
+    ++launches;
+    check_launch("gradient");
+    const double E = read_energy();
+    have_lin = true;
+    have_dm1 = false;
+    if (!std::isfinite(E)) {
+      *err = "energy is not finite";
+      throw Fail{LDDMM_ENONFINITE};
+    }
+    return E;
+  }
+
+  double gradient(const void* v0, void* g) {
+    load_bl(v0, vsol);
+    const double E = gradient_dev(vsol, gbuf);
+    store_bl(gbuf, g);
+    sync("gradient output");
+    return E;
+  }
+
+  void invalidate_graph() {
+    if (hv_exec) {
+      cudaGraphExecDestroy(hv_exec);
+      hv_exec = nullptr;
+    }
+  }
+
+  // Hessian-vector product with input already in dvh[0]; result in vout
+  void hessvec_dev() {
+    if (!have_lin) {
+      *err = "no linearisation point (call lddmm_gradient first)";
+      throw Fail{LDDMM_ESTATE};
+    }
+    if (opts.use_graphs) {
+      if (!hv_exec) build_graph();
+      cuda(cudaEventRecord(ev, st), "event record");
+      cuda(cudaStreamWaitEvent(cap, ev, 0), "wait");
+      cuda(cudaGraphLaunch(hv_exec, cap), "graph launch");
+      cuda(cudaEventRecord(ev, cap), "event record");
+      cuda(cudaStreamWaitEvent(st, ev, 0), "wait");
+      launches += hv_nodes;
+    } else {
+      enqueue_hessvec();
+    }
+    have_dm1 = true;
+  }
+
+  void build_graph() {
+    cudaStream_t user = st;
+    st = cap;
+    const long long before = launches;
+    cudaGraph_t g = nullptr;
+    cuda(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    try {
+      enqueue_hessvec();
+    } catch (...) {
+      cudaStreamEndCapture(cap, &g);
+      if (g) cudaGraphDestroy(g);
+      st = user;
+      throw;
+    }
+    st = user;
+    cuda(cudaStreamEndCapture(cap, &g), "end capture");
+    hv_nodes = launches - before;
+    launches = before;
+    cudaError_t e = cudaGraphInstantiate(&hv_exec, g, 0);
+    cudaGraphDestroy(g);
+    cuda(e, "graph instantiate");
+  }
+
+  void hessvec(const void* dv, void* out) {
+    if (!have_lin) {
+      *err = "no linearisation point (call lddmm_gradient first)";
+      throw Fail{LDDMM_ESTATE};
+    }
+    load_bl(dv, dvh);
+    hessvec_dev();
+    store_bl(vout, out);
+    sync("hessvec");
+  }
+
+  void gn_solve(void* v0, int n_gn, int n_pcg, lddmm_report* rep) {
+    need_images();
+    load_bl(v0, vsol);
+    lddmm_report r{};
+    if (rep) {
+      r.E_hist = rep->E_hist;
+      r.eps_hist = rep->eps_hist;
+      r.pcg_hist = rep->pcg_hist;
+    }
+    const double c = opts.armijo_c;
+    const size_t bytes = (size_t)3 * Kvol * sizeof(C);
+    for (int it = 0; it < n_gn; ++it) {
+      const double E = gradient_dev(vsol, gbuf);
+      const double gn = std::sqrt(dot_V(gbuf, gbuf));
+      if (it == 0) {
+        r.E_initial = E;
+        r.gnorm_initial = gn;
+      }
+      r.gnorm_final = gn;
+      if (r.E_hist) r.E_hist[it] = E;
+      // CG in the V inner product on H p = -g (Eq. 45)
+      cuda(cudaMemsetAsync(px, 0, bytes, st), "memset");
+      axpby<T>(pr, -1.0, gbuf, 0.0, nullptr, 3 * Kvol, st);
+      cuda(cudaMemcpyAsync(pd, pr, bytes, cudaMemcpyDeviceToDevice, st), "copy");
+      ++launches;
+      double rho = dot_V(pr, pr);
+      const double bnorm = std::sqrt(rho);
+      int its = 0;
+      for (int k = 1; k <= n_pcg; ++k) {
+        cuda(cudaMemcpyAsync(dvh, pd, bytes, cudaMemcpyDeviceToDevice, st), "copy");
+        hessvec_dev();
+        cuda(cudaMemcpyAsync(pq, vout, bytes, cudaMemcpyDeviceToDevice, st), "copy");
+        const double dq = dot_V(pd, pq);
+        if (!(dq > 0.0)) {
+          if (k == 1) cuda(cudaMemcpyAsync(px, pd, bytes, cudaMemcpyDeviceToDevice, st), "copy");
+          its = k - 1;
+          break;
+        }
+        const double a = rho / dq;
+        axpby<T>(px, 1.0, px, a, pd, 3 * Kvol, st);
+        axpby<T>(pr, 1.0, pr, -a, pq, 3 * Kvol, st);
+        launches += 2;
+        const double rho_new = dot_V(pr, pr);
+        its = k;
+        if (std::sqrt(rho_new) <= opts.pcg_tol * bnorm) break;
+        axpby<T>(pd, 1.0, pr, rho_new / rho, pd, 3 * Kvol, st);
+        ++launches;
+        rho = rho_new;
+      }
+      r.pcg_iters += its;
+      if (r.pcg_hist) r.pcg_hist[it] = its;
+      // Armijo backtracking along p (Eq. 44 with the step sign read as +)
+      const double slope = dot_V(gbuf, px);
+      double eps = 1.0;
+      bool ok = false;
+      for (int h = 0; h <= opts.max_halvings; ++h) {
+        axpby<T>(vtry, 1.0, vsol, eps, px, 3 * Kvol, st);
+        ++launches;
+        const double Et = energy_dev(vtry);
+        if (Et <= E + c * eps * slope) {
+          ok = true;
+          break;
+        }
+        eps *= 0.5;
+      }
+      if (!ok) {
+        r.ls_failed = 1;
+        r.gn_iters = it;
+        break;
+      }
+      if (r.eps_hist) r.eps_hist[it] = eps;
+      cuda(cudaMemcpyAsync(vsol, vtry, bytes, cudaMemcpyDeviceToDevice, st), "copy");
+      r.gn_iters = it + 1;
+    }
+    r.E_final = energy_dev(vsol);
+    store_bl(vsol, v0);
+    sync("gn_solve");
+    if (rep) *rep = r;
+  }
+
+  // component calls ---------------------------------------------------------
+  void iota_call(const void* a, int ncomp, void* out) {
+    for (int c0 = 0; c0 < ncomp; c0 += 3) {
+      const int nc = std::min(3, ncomp - c0);
+      cuda(cudaMemcpyAsync(vin, (const C*)a + (long long)c0 * Kvol, (size_t)nc * Kvol * sizeof(C),
+                           cudaMemcpyDefault, st), "copy");
+      hermitianize<T>(vin, px, nc, K, st);
+      ++launches;
+      IotaDesc<T> d{};
+      d.nf = nc;
+      for (int c = 0; c < nc; ++c) {
+        d.src[c] = px + c * Kvol;
+        d.dst[c] = fterm + c * Nvol;
+        d.deriv[c] = -1;
+        d.applyL[c] = 0;
+      }
+      iota_batch<T>(full, d, Lhat, T1, T2, st);
+      launches += kIotaLaunches;
+      check_launch("iota");
+      cuda(cudaMemcpyAsync((T*)out + (long long)c0 * Nvol, fterm, (size_t)nc * Nvol * sizeof(T),
+                           cudaMemcpyDefault, st), "copy");
+    }
+    sync("iota");
+  }
+
+  void pi_call(const void* f, int ncomp, void* out) {
+    for (int c0 = 0; c0 < ncomp; c0 += 3) {
+      const int nc = std::min(3, ncomp - c0);
+      cuda(cudaMemcpyAsync(fterm, (const T*)f + (long long)c0 * Nvol, (size_t)nc * Nvol * sizeof(T),
+                           cudaMemcpyDefault, st), "copy");
+      PiSrc<T> ps{};
+      ps.nf = nc;
+      for (int c = 0; c < nc; ++c) ps.src[c] = fterm + c * Nvol;
+      PiEpi<T> e = epi(nc, 1);
+      e.grp[0] = 0;
+      e.coef[0] = (T)(1.0 / (double)Nvol);
+      e.applyK[0] = 0;
+      add_out(e, vout, 0, 1.0, {});
+      pi_batch<T>(full, ps, e, Lhat, T1, T2, st);
+      launches += kPiLaunches;
+      check_launch("pi");
+      cuda(cudaMemcpyAsync((C*)out + (long long)c0 * Kvol, vout, (size_t)nc * Kvol * sizeof(C),
+                           cudaMemcpyDefault, st), "copy");
+    }
+    sync("pi");
+  }
+
+  void ad_dagger_call(const void* v, const void* u, void* out) {
+    load_bl(v, px);
+    load_bl(u, pr);
+    PiEpi<T> e = epi(3, 1);
+    e.grp[0] = 0;
+    e.coef[0] = (T)(1.0 / (double)Mvol);
+    e.applyK[0] = 1;
+    add_out(e, vout, 0, 1.0, {});
+    eval(PW_F, X, px, pr, e);       // P(v, L u) with v-fields from px, L-fields from pr
+    store_bl(vout, out);
+    sync("ad_dagger");
+  }
+
+  void ad_call(const void* v, const void* w, void* out) {
+    load_bl(v, px);
+    load_bl(w, pr);
+    T* vslot = slot(trial, 0);
+    iota_batch<T>(pad, block24(px, px, vslot), Lhat, T1, T2, st);
+    iota_batch<T>(pad, block24(pr, pr, X), Lhat, T1, T2, st);
+    pointwise<T>(PW_GT, X, vslot, P, Mvol, st);
+    PiSrc<T> ps{};
+    ps.nf = 3;
+    for (int c = 0; c < 3; ++c) ps.src[c] = P + (6 + c) * Mvol;
+    PiEpi<T> e = epi(3, 1);
+    e.grp[0] = 0;
+    e.coef[0] = (T)(1.0 / (double)Mvol);
+    e.applyK[0] = 0;
+    add_out(e, vout, 0, 1.0, {});
+    pi_batch<T>(pad, ps, e, Lhat, T1, T2, st);
+    launches += 2 * kIotaLaunches + 1 + kPiLaunches;
+    check_launch("ad");
+    store_bl(vout, out);
+    sync("ad");
+  }
+
+  void shoot_call(const void* v0, void* v1) {
+    load_bl(v0, trial.vh);
+    shoot(trial);
+    store_bl(vec(trial.vh, Nt), v1);
+    sync("shoot");
+  }
+
+  void transport_call(const void* v0, void* m1) {
+    need_images();
+    load_bl(v0, trial.vh);
+    forward(trial);
+    cuda(cudaMemcpyAsync(m1, trial.mh + (long long)Nt * Nvol, (size_t)Nvol * sizeof(T),
+                         cudaMemcpyDefault, st), "copy m1");
+    sync("transport");
+  }
+
+  void last_dm1(void* out) {
+    if (!have_dm1) {
+      *err = "no Hessian-vector product computed at this linearisation point";
+      throw Fail{LDDMM_ESTATE};
+    }
+    cuda(cudaMemcpyAsync(out, dm[Nt & 1], (size_t)Nvol * sizeof(T), cudaMemcpyDefault, st), "copy dm1");
+    sync("dm1");
+  }
+};
+
+template <typename F>
+int guarded(lddmm_ctx* ctx, F&& f) {
+  if (!ctx) return LDDMM_EINVAL;
+  try {
+    f();
+    return LDDMM_OK;
+  } catch (const Fail& e) {
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    ctx->err = "host allocation failed";
+    return LDDMM_ENOMEM;
+  } catch (...) {
+    ctx->err = "unexpected exception";
+    return LDDMM_ECUDA;
+  }
+}
+
+template <typename Fn>
+int dispatch(lddmm_ctx* ctx, Fn&& fn) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (ctx->precision == LDDMM_FP64)
+    return guarded(ctx, [&] { fn(*static_cast<Impl<double>*>(ctx->impl)); });
+  return guarded(ctx, [&] { fn(*static_cast<Impl<float>*>(ctx->impl)); });
+}
+
+bool bad_ptr(lddmm_ctx* ctx, const void* p, const char* name) {
+  if (p) return false;
+  ctx->err = std::string("null pointer: ") + name;
+  return true;
+}
+
+}  // namespace
+}  // namespace lddmm
+
+using lddmm::Impl;
+using lddmm::bad_ptr;
+
+extern "C" {
+
+void lddmm_default_opts(lddmm_opts* o) {
+  if (!o) return;
+  o->precision = LDDMM_FP32;
+  o->stream = nullptr;
+  o->pcg_tol = 1e-12;
+  o->armijo_c = 1e-4;
+  o->max_halvings = 10;
+  o->use_graphs = 1;
+}
+
+int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, double alpha, int s,
+                 double sigma, int Nt, const lddmm_opts* opts) {
+  if (!out) return LDDMM_EINVAL;
+  *out = nullptr;
+  if ((ndim != 2 && ndim != 3) || !grid || !K || !(alpha > 0) || s < 1 || !(sigma > 0) || Nt < 1)
+    return LDDMM_EINVAL;
+  for (int j = 0; j < ndim; ++j) {
+    if (grid[j] < 2 || K[j] < 2 || (K[j] & 1) || K[j] > grid[j] || grid[j] > (1 << 16))
+      return LDDMM_EINVAL;
+  }
+  lddmm_opts o;
+  lddmm_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.precision != LDDMM_FP32 && o.precision != LDDMM_FP64) return LDDMM_EINVAL;
+  lddmm_ctx* ctx = new (std::nothrow) lddmm_ctx();
+  if (!ctx) return LDDMM_ENOMEM;
+  ctx->precision = o.precision;
+  ctx->impl = nullptr;
+  int rc;
+  if (o.precision == LDDMM_FP64) {
+    auto* im = new (std::nothrow) Impl<double>();
+    if (!im) { delete ctx; return LDDMM_ENOMEM; }
+    im->err = &ctx->err;
+    ctx->impl = im;
+    rc = lddmm::guarded(ctx, [&] { im->create(ndim, grid, K, alpha, s, sigma, Nt, o); });
+  } else {
+    auto* im = new (std::nothrow) Impl<float>();
+    if (!im) { delete ctx; return LDDMM_ENOMEM; }
+    im->err = &ctx->err;
+    ctx->impl = im;
+    rc = lddmm::guarded(ctx, [&] { im->create(ndim, grid, K, alpha, s, sigma, Nt, o); });
+  }
+  if (rc != LDDMM_OK) {
+    lddmm_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return LDDMM_OK;
+}
+
+int lddmm_set_images(lddmm_ctx* ctx, const void* I0, const void* I1) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, I0, "I0") || bad_ptr(ctx, I1, "I1")) return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) { im.set_images(I0, I1); });
+}
+
+int lddmm_energy(lddmm_ctx* ctx, const void* v0, double* E) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, v0, "v0") || bad_ptr(ctx, E, "E_out")) return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) { *E = im.energy(v0); });
+}
+
+int lddmm_gradient(lddmm_ctx* ctx, const void* v0, void* g, double* E) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, v0, "v0") || bad_ptr(ctx, g, "g_out")) return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) {
+    const double e = im.gradient(v0, g);
+    if (E) *E = e;
+  });
+}
+
+int lddmm_hessvec(lddmm_ctx* ctx, const void* dv, void* out) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, dv, "dv") || bad_ptr(ctx, out, "Hdv_out")) return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) { im.hessvec(dv, out); });
+}
+
+int lddmm_gn_solve(lddmm_ctx* ctx, void* v0, int n_gn, int n_pcg, lddmm_report* rep) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, v0, "v0_inout")) return LDDMM_EINVAL;
+  if (n_gn < 0 || n_pcg < 1) {
+    ctx->err = "n_gn must be >= 0 and n_pcg >= 1";
+    return LDDMM_EINVAL;
+  }
+  return lddmm::dispatch(ctx, [&](auto& im) { im.gn_solve(v0, n_gn, n_pcg, rep); });
+}
+
+int lddmm_iota(lddmm_ctx* ctx, const void* a, int ncomp, void* f) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, a, "a") || bad_ptr(ctx, f, "f_out") || ncomp < 1) return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) { im.iota_call(a, ncomp, f); });
+}
+
+int lddmm_pi(lddmm_ctx* ctx, const void* f, int ncomp, void* a) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, f, "f") || bad_ptr(ctx, a, "a_out") || ncomp < 1) return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) { im.pi_call(f, ncomp, a); });
+}
+
+int lddmm_ad_dagger(lddmm_ctx* ctx, const void* v, const void* u, void* out) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, v, "v") || bad_ptr(ctx, u, "u") || bad_ptr(ctx, out, "out")) return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) { im.ad_dagger_call(v, u, out); });
+}
+
+int lddmm_ad(lddmm_ctx* ctx, const void* v, const void* w, void* out) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, v, "v") || bad_ptr(ctx, w, "w") || bad_ptr(ctx, out, "out")) return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) { im.ad_call(v, w, out); });
+}
+
+int lddmm_shoot(lddmm_ctx* ctx, const void* v0, void* v1) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, v0, "v0") || bad_ptr(ctx, v1, "v1_out")) return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) { im.shoot_call(v0, v1); });
+}
+
+int lddmm_transport(lddmm_ctx* ctx, const void* v0, void* m1) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, v0, "v0") || bad_ptr(ctx, m1, "m1_out")) return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) { im.transport_call(v0, m1); });
+}
+
+int lddmm_last_dm1(lddmm_ctx* ctx, void* out) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, out, "dm1_out")) return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) { im.last_dm1(out); });
+}
+
+long long lddmm_kernel_count(const lddmm_ctx* ctx) {
+  if (!ctx || !ctx->impl) return 0;
+  if (ctx->precision == LDDMM_FP64) return static_cast<const Impl<double>*>(ctx->impl)->launches;
+  return static_cast<const Impl<float>*>(ctx->impl)->launches;
+}
+
+const char* lddmm_last_error(const lddmm_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+void lddmm_destroy(lddmm_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->impl) {
+    if (ctx->precision == LDDMM_FP64) {
+      auto* im = static_cast<Impl<double>*>(ctx->impl);
+      im->release();
+      delete im;
+    } else {
+      auto* im = static_cast<Impl<float>*>(ctx->impl);
+      im->release();
+      delete im;
+    }
+  }
+  delete ctx;
+}
+
+}  // extern "C"

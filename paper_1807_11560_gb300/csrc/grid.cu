@@ -1,0 +1,396 @@
+// Grid-point kernels of the GB300 LDDMM library (sm_103a):
+//   * bracket products of ad~* and ad~ on the padded grid (Eqs. 4, 48, 49),
+//   * semi-Lagrangian state and incremental-state transport on the image grid
+//     (Eqs. 52 and 31),
+//   * terminal adjoint fields lambda(1) grad m(1) (Eq. 55, Eq. 58 under GN),
+//   * band-vector updates and deterministic FP64 reductions (Eq. 47, Eq. 50).
+// One thread per grid point or band slot; the transport kernels are bound by
+// HBM traffic (coalesced streams plus an L1/L2-served 8-corner gather).
+#include "internal.h"
+
+namespace lddmm {
+namespace {
+
+constexpr int kThreads = 256;
+inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+__device__ __forceinline__ bool nyq(int q, int K) { return (K % 2 == 0) && (2 * q == K); }
+
+// ---- bracket products --------------------------------------------------------
+// Field block layout: a[c] at c, Da[c][j] = d_j a_c at 3 + 3c + j.
+// P(a, m)_i = sum_j Da[j][i] m_j + sum_j Dm[i][j] a_j + m_i div a   (ad* bracket, Eq. 4)
+// Q(a, w)_i = sum_j Da[i][j] w_j - Dw[i][j] a_j                      (ad bracket, Eq. 49)
+template <typename T>
+__device__ __forceinline__ void bracketP(const T* a, const T* m, T* out) {
+  const T* Da = a + 3;
+  const T* Dm = m + 3;
+  const T div = Da[0] + Da[4] + Da[8];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T s = m[i] * div;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s = fma(Da[3 * j + i], m[j], fma(Dm[3 * i + j], a[j], s));
+    out[i] += s;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void bracketQ(const T* a, const T* w, T* out) {
+  const T* Da = a + 3;
+  const T* Dw = w + 3;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s = fma(Da[3 * i + j], w[j], fma(-Dw[3 * i + j], a[j], s));
+    out[i] += s;
+  }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_pointwise(const T* __restrict__ X, const T* __restrict__ Cc, T* __restrict__ P, long long vol) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= vol) return;
+  T cv[12], cl[12];
+#pragma unroll
+  for (int f = 0; f < 12; ++f) { cv[f] = Cc[f * vol + i]; cl[f] = Cc[(12 + f) * vol + i]; }
+  if (MODE == PW_F) {
+    T o[3] = {T(0), T(0), T(0)};
+    bracketP(cv, cl, o);                        // P(v, L v)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) P[c * vol + i] = o[c];
+  } else {
+    T xv[12], xl[12];
+#pragma unroll
+    for (int f = 0; f < 12; ++f) { xv[f] = X[f * vol + i]; xl[f] = X[(12 + f) * vol + i]; }
+    if (MODE == PW_T) {
+      T o[3] = {T(0), T(0), T(0)};
+      bracketP(xv, cl, o);                      // P(dv, L v)
+      bracketP(cv, xl, o);                      // P(v, L dv)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) P[c * vol + i] = o[c];
+    } else {
+      T a[3] = {T(0), T(0), T(0)}, b[3] = {T(0), T(0), T(0)}, q[3] = {T(0), T(0), T(0)};
+      bracketP(cv, xl, a);                      // P(v, L U)
+      bracketP(xv, cl, b);                      // P(W, L v)
+      bracketQ(cv, xv, q);                      // Q(v, W)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        P[c * vol + i] = a[c];
+        P[(3 + c) * vol + i] = b[c];
+        P[(6 + c) * vol + i] = q[c];
+      }
+    }
+  }
+}
+
+// ---- periodic trilinear interpolation ------------------------------------------
+// Cell of the point ix - dsp on an axis of n nodes: lower node c0, upper c1,
+// weight w of the upper node.  The foot point is kept as integer index plus a
+// small offset, never as an absolute coordinate.
+template <typename T>
+__device__ __forceinline__ void cell(int ix, T dsp, int n, int& c0, int& c1, T& w) {
+  const T nd = -dsp;
+  T fl = floor(nd);
+  w = nd - fl;
+  // a non-finite or absurd displacement keeps its NaN weight but a safe index
+  if (!(fabs(fl) < T(1e6))) fl = T(0);
+  int c = (ix + (int)fl) % n;
+  if (c < 0) c += n;
+  c0 = c;
+  c1 = (c + 1 == n) ? 0 : c + 1;
+}
+
+template <typename T>
+__device__ __forceinline__ void corners(const int* c0, const int* c1, int n2, int n3, long long* o) {
+  const long long a0 = (long long)c0[0] * n2, a1 = (long long)c1[0] * n2;
+  o[0] = (a0 + c0[1]) * n3 + c0[2];
+  o[1] = (a0 + c0[1]) * n3 + c1[2];
+  o[2] = (a0 + c1[1]) * n3 + c0[2];
+  o[3] = (a0 + c1[1]) * n3 + c1[2];
+  o[4] = (a1 + c0[1]) * n3 + c0[2];
+  o[5] = (a1 + c0[1]) * n3 + c1[2];
+  o[6] = (a1 + c1[1]) * n3 + c0[2];
+  o[7] = (a1 + c1[1]) * n3 + c1[2];
+}
+
+template <typename T>
+__device__ __forceinline__ T trilin(const T* __restrict__ f, const long long* o, const T* w) {
+  const T u0 = f[o[0]] + w[2] * (f[o[1]] - f[o[0]]);
+  const T u1 = f[o[2]] + w[2] * (f[o[3]] - f[o[2]]);
+  const T u2 = f[o[4]] + w[2] * (f[o[5]] - f[o[4]]);
+  const T u3 = f[o[6]] + w[2] * (f[o[7]] - f[o[6]]);
+  const T v0 = u0 + w[1] * (u1 - u0);
+  const T v1 = u2 + w[1] * (u3 - u2);
+  return v0 + w[0] * (v1 - v0);
+}
+
+__device__ __forceinline__ void unflat(long long idx, int n2, int n3, int* ix) {
+  ix[2] = (int)(idx % n3);
+  const long long r = idx / n3;
+  ix[1] = (int)(r % n2);
+  ix[0] = (int)(r / n2);
+}
+
+// central difference d_j m at grid index ix (periodic), in unit-domain units
+template <typename T>
+__device__ __forceinline__ T cdiff(const T* __restrict__ m, const int* ix, int j, Dims g) {
+  const int n[3] = {g.n1, g.n2, g.n3};
+  int p[3] = {ix[0], ix[1], ix[2]}, q[3] = {ix[0], ix[1], ix[2]};
+  p[j] = (ix[j] + 1 == n[j]) ? 0 : ix[j] + 1;
+  q[j] = (ix[j] == 0) ? n[j] - 1 : ix[j] - 1;
+  const T mp = m[((long long)p[0] * g.n2 + p[1]) * g.n3 + p[2]];
+  const T mq = m[((long long)q[0] * g.n2 + q[1]) * g.n3 + q[2]];
+  return (mp - mq) * (T(0.5) * T(n[j]));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_transport(const T* __restrict__ m, const T* __restrict__ vn, const T* __restrict__ vc,
+            T* __restrict__ mn, T* __restrict__ off, Dims g, T dt) {
+  const long long vol = g.vol();
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= vol) return;
+  int ix[3];
+  unflat(idx, g.n2, g.n3, ix);
+  const int n[3] = {g.n1, g.n2, g.n3};
+  T a[3], c0w[3];
+  int c0[3], c1[3];
+  long long o[8];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    a[j] = vn[j * vol + idx];
+    cell(ix[j], dt * T(n[j]) * a[j], n[j], c0[j], c1[j], c0w[j]);
+  }
+  corners<T>(c0, c1, g.n2, g.n3, o);
+  T dsp[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const T u = trilin(vc + j * vol, o, c0w);
+    dsp[j] = T(0.5) * dt * T(n[j]) * (a[j] + u);
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) cell(ix[j], dsp[j], n[j], c0[j], c1[j], c0w[j]);
+  corners<T>(c0, c1, g.n2, g.n3, o);
+  mn[idx] = trilin(m, o, c0w);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) off[j * vol + idx] = dsp[j];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_grad_dot(const T* __restrict__ m, const T* __restrict__ dv, T* __restrict__ s, Dims g) {
+  const long long vol = g.vol();
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= vol) return;
+  int ix[3];
+  unflat(idx, g.n2, g.n3, ix);
+  T acc = T(0);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) acc = fma(cdiff(m, ix, j, g), dv[j * vol + idx], acc);
+  s[idx] = acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_inc_step(const T* __restrict__ dm, const T* __restrict__ s, const T* __restrict__ mnext,
+           const T* __restrict__ dvn, const T* __restrict__ off, T* __restrict__ dmn,
+           T* __restrict__ sn, Dims g, T dt) {
+  const long long vol = g.vol();
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= vol) return;
+  int ix[3];
+  unflat(idx, g.n2, g.n3, ix);
+  const int n[3] = {g.n1, g.n2, g.n3};
+  T snew = T(0);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) snew = fma(cdiff(mnext, ix, j, g), dvn[j * vol + idx], snew);
+  int c0[3], c1[3];
+  T w[3];
+  long long o[8];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) cell(ix[j], off[j * vol + idx], n[j], c0[j], c1[j], w[j]);
+  corners<T>(c0, c1, g.n2, g.n3, o);
+  const T dmi = dm ? trilin(dm, o, w) : T(0);
+  const T si = trilin(s, o, w);
+  dmn[idx] = dmi - T(0.5) * dt * (si + snew);
+  sn[idx] = snew;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_terminal(const T* __restrict__ m, const T* __restrict__ y, int diff, T coef, T* __restrict__ out,
+           Dims g) {
+  const long long vol = g.vol();
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= vol) return;
+  int ix[3];
+  unflat(idx, g.n2, g.n3, ix);
+  const T r = coef * (diff ? (m[idx] - y[idx]) : y[idx]);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) out[j * vol + idx] = r * cdiff(m, ix, j, g);
+}
+
+// ---- band vectors -----------------------------------------------------------------
+template <typename T>
+__global__ void k_hermitianize(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int ncomp,
+                               Band b) {
+  const long long kvol = b.vol();
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ncomp * kvol) return;
+  const long long c = idx / kvol;
+  const long long r = idx % kvol;
+  const int k3 = (int)(r % b.k3);
+  const int k2 = (int)((r / b.k3) % b.k2);
+  const int k1 = (int)(r / ((long long)b.k2 * b.k3));
+  cplx<T> v{T(0), T(0)};
+  if (!(nyq(k1, b.k1) || nyq(k2, b.k2) || nyq(k3, b.k3))) {
+    const long long m = c * kvol +
+        (((long long)((b.k1 - k1) % b.k1) * b.k2 + (b.k2 - k2) % b.k2) * b.k3 + (b.k3 - k3) % b.k3);
+    const cplx<T> a = in[idx], am = in[m];
+    v.x = T(0.5) * (a.x + am.x);
+    v.y = T(0.5) * (a.y - am.y);
+  }
+  out[idx] = v;
+}
+
+template <typename T>
+__global__ void k_axpby(cplx<T>* out, T a, const cplx<T>* x, T bc, const cplx<T>* y, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  cplx<T> v = x[i];
+  v.x *= a;
+  v.y *= a;
+  if (y) {
+    v.x = fma(bc, y[i].x, v.x);
+    v.y = fma(bc, y[i].y, v.y);
+  }
+  out[i] = v;
+}
+
+// ---- deterministic FP64 reductions ------------------------------------------------
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = (threadIdx.x < kThreads / 32) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_sumsq_diff(const T* __restrict__ a, const T* __restrict__ b, long long n, double* partial) {
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double d = (double)a[i] - (double)b[i];
+    acc = fma(d, d, acc);
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_inner_V(const cplx<T>* __restrict__ a, const cplx<T>* __restrict__ b, const T* __restrict__ L,
+          long long kvol, long long n, double* partial) {
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double l = (double)L[i % kvol];
+    acc = fma(l, (double)a[i].x * (double)b[i].x + (double)a[i].y * (double)b[i].y, acc);
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kThreads) k_finalize(const double* partial, int n, double* out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += kThreads) acc += partial[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+}  // namespace
+
+template <typename T>
+void pointwise(PwMode mode, const T* X, const T* C, T* P, long long vol, cudaStream_t st) {
+  switch (mode) {
+    case PW_F: k_pointwise<T, PW_F><<<blocks_for(vol), kThreads, 0, st>>>(X, C, P, vol); break;
+    case PW_T: k_pointwise<T, PW_T><<<blocks_for(vol), kThreads, 0, st>>>(X, C, P, vol); break;
+    case PW_GT: k_pointwise<T, PW_GT><<<blocks_for(vol), kThreads, 0, st>>>(X, C, P, vol); break;
+  }
+}
+
+template <typename T>
+void transport_step(const T* m, const T* vnext, const T* vcur, T* mnext, T* off, Dims g, double dt,
+                    cudaStream_t st) {
+  k_transport<T><<<blocks_for(g.vol()), kThreads, 0, st>>>(m, vnext, vcur, mnext, off, g, (T)dt);
+}
+
+template <typename T>
+void grad_dot(const T* m, const T* dv, T* s, Dims g, cudaStream_t st) {
+  k_grad_dot<T><<<blocks_for(g.vol()), kThreads, 0, st>>>(m, dv, s, g);
+}
+
+template <typename T>
+void inc_step(const T* dm, const T* s, const T* mnext, const T* dvnext, const T* off, T* dmnext,
+              T* snext, Dims g, double dt, cudaStream_t st) {
+  k_inc_step<T><<<blocks_for(g.vol()), kThreads, 0, st>>>(dm, s, mnext, dvnext, off, dmnext, snext, g,
+                                                         (T)dt);
+}
+
+template <typename T>
+void terminal_field(const T* m, const T* y, int diff, double coef, T* out, Dims g, cudaStream_t st) {
+  k_terminal<T><<<blocks_for(g.vol()), kThreads, 0, st>>>(m, y, diff, (T)coef, out, g);
+}
+
+template <typename T>
+void hermitianize(const cplx<T>* in, cplx<T>* out, int ncomp, Band b, cudaStream_t st) {
+  k_hermitianize<T><<<blocks_for(ncomp * b.vol()), kThreads, 0, st>>>(in, out, ncomp, b);
+}
+
+template <typename T>
+void axpby(cplx<T>* out, double a, const cplx<T>* x, double bcoef, const cplx<T>* y, long long n,
+           cudaStream_t st) {
+  k_axpby<T><<<blocks_for(n), kThreads, 0, st>>>(out, (T)a, x, (T)bcoef, y, n);
+}
+
+template <typename T>
+void sum_sq_diff(const T* a, const T* b, long long n, double* partial, double* out, cudaStream_t st) {
+  k_sumsq_diff<T><<<kReduceBlocks, kThreads, 0, st>>>(a, b, n, partial);
+  k_finalize<<<1, kThreads, 0, st>>>(partial, kReduceBlocks, out);
+}
+
+template <typename T>
+void inner_V(const cplx<T>* a, const cplx<T>* b, const T* Lhat, int ncomp, long long kvol,
+             double* partial, double* out, cudaStream_t st) {
+  k_inner_V<T><<<kReduceBlocks, kThreads, 0, st>>>(a, b, Lhat, kvol, ncomp * kvol, partial);
+  k_finalize<<<1, kThreads, 0, st>>>(partial, kReduceBlocks, out);
+}
+
+#define LDDMM_INST(T)                                                                              \
+  template void pointwise<T>(PwMode, const T*, const T*, T*, long long, cudaStream_t);           \
+  template void transport_step<T>(const T*, const T*, const T*, T*, T*, Dims, double,            \
+                                  cudaStream_t);                                                 \
+  template void grad_dot<T>(const T*, const T*, T*, Dims, cudaStream_t);                         \
+  template void inc_step<T>(const T*, const T*, const T*, const T*, const T*, T*, T*, Dims,      \
+                            double, cudaStream_t);                                               \
+  template void terminal_field<T>(const T*, const T*, int, double, T*, Dims, cudaStream_t);      \
+  template void hermitianize<T>(const cplx<T>*, cplx<T>*, int, Band, cudaStream_t);             \
+  template void axpby<T>(cplx<T>*, double, const cplx<T>*, double, const cplx<T>*, long long,    \
+                         cudaStream_t);                                                          \
+  template void sum_sq_diff<T>(const T*, const T*, long long, double*, double*, cudaStream_t);   \
+  template void inner_V<T>(const cplx<T>*, const cplx<T>*, const T*, int, long long, double*,    \
+                           double*, cudaStream_t);
+LDDMM_INST(float)
+LDDMM_INST(double)
+
+}  // namespace lddmm

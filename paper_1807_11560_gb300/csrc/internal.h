@@ -1,0 +1,148 @@
+// Internal declarations of the GB300 LDDMM library: data layouts, transform
+// plans, launch descriptors and kernel launchers.  Not part of the C interface.
+//
+// Internally every problem is three-dimensional with three velocity
+// components: a 2D problem is the slab N_3 = 1, K_3 = 1 with a zero third
+// component (the 3D formulas then reduce exactly to the 2D ones).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace lddmm {
+
+template <typename T> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+template <typename T> using cplx = typename CplxOf<T>::type;
+
+// Grid sizes of one transform plan: the image grid N or the padded product
+// grid M = ceil(3K/2).
+struct Dims {
+  int n1, n2, n3;
+  __host__ __device__ long long vol() const { return (long long)n1 * n2 * n3; }
+};
+
+// Band sizes K_j and h1 = number of non-negative k1 slots kept by the
+// Hermitian half-spectrum transforms (K_1/2, or 1 for a degenerate axis).
+struct Band {
+  int k1, k2, k3, h1;
+  __host__ __device__ long long vol() const { return (long long)k1 * k2 * k3; }
+};
+
+// Twiddle tables of one (grid, band) pair, device resident, precision T.
+//   E3f[k3][x3] = exp(+2 pi i f(k3) x3 / G3)          (iota, axis 3)
+//   E2f[k2][x2] = exp(+2 pi i f(k2) x2 / G2)          (iota, axis 2)
+//   E1f[h][x1]  = w(h) exp(+2 pi i h x1 / G1), w = 1 (h = 0) or 2
+//   E1b[x1][h]  = exp(-2 pi i h x1 / G1)              (pi, axis 1)
+//   E2b[x2][k2] = exp(-2 pi i f(k2) x2 / G2)
+//   E3b[x3][k3] = exp(-2 pi i f(k3) x3 / G3)
+template <typename T>
+struct Plan {
+  Dims g;
+  Band b;
+  cplx<T>* E3f;
+  cplx<T>* E2f;
+  cplx<T>* E1f;
+  cplx<T>* E1b;
+  cplx<T>* E2b;
+  cplx<T>* E3b;
+};
+
+// iota batch: field f is iota of (multiplier x one scalar band slab), where
+// the multiplier is L^(k) if applyL and 2 pi i f_deriv(k) if deriv >= 0.
+constexpr int kMaxIota = 36;
+template <typename T>
+struct IotaDesc {
+  int nf;
+  const cplx<T>* src[kMaxIota];   // scalar band slab [K1][K2][K3]
+  T* dst[kMaxIota];               // grid field [G1][G2][G3]
+  signed char deriv[kMaxIota];    // -1 or axis 0..2
+  signed char applyL[kMaxIota];
+};
+
+// pi batch inputs: nf real grid fields.
+constexpr int kMaxPi = 36;
+template <typename T>
+struct PiSrc {
+  int nf;
+  const T* src[kMaxPi];
+};
+
+// Epilogue of the last pi stage.  The pi fields are indexed f = o*ncomp + c
+// (o < nper).  For band slot k of component c:
+//   R_r(k) = sum_{o: grp[o]==r} coef[o] * (applyK[o] ? 1/L^(k) : 1) * pi_o(k)
+//   dst_j(k) = cR[j] * R_{r[j]}(k) + sum_i cX[j][i] * X[j][i](k)
+// coef includes the 1/(G1 G2 G3) normalisation.  X and dst are band vectors
+// [ncomp][K1][K2][K3]; outputs are written Hermitian with zero Nyquist slots.
+constexpr int kMaxPer = 3, kMaxOut = 4, kMaxX = 4;
+template <typename T>
+struct PiEpi {
+  int ncomp, nper;
+  int grp[kMaxPer];
+  T coef[kMaxPer];
+  int applyK[kMaxPer];
+  int nout;
+  cplx<T>* dst[kMaxOut];
+  int r[kMaxOut];
+  T cR[kMaxOut];
+  int nx[kMaxOut];
+  const cplx<T>* X[kMaxOut][kMaxX];
+  T cX[kMaxOut][kMaxX];
+};
+
+// ---- transforms (dft.cu) --------------------------------------------------
+// Scratch: T1 holds [F][h1][K2][G3] complex, T2 holds [F][h1][G2][G3] complex.
+template <typename T>
+void iota_batch(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat,
+                cplx<T>* T1, cplx<T>* T2, cudaStream_t st);
+template <typename T>
+void pi_batch(const Plan<T>& p, const PiSrc<T>& s, const PiEpi<T>& e, const T* Lhat,
+              cplx<T>* T1, cplx<T>* T2, cudaStream_t st);
+// number of kernel launches of one iota_batch / pi_batch call
+constexpr int kIotaLaunches = 3, kPiLaunches = 3;
+
+// ---- grid kernels (grid.cu) -----------------------------------------------
+enum PwMode { PW_F = 0, PW_T = 1, PW_GT = 2 };
+// Pointwise bracket products on the padded grid.  X: 24 fields of this
+// evaluation, C: 24 cached fields of the stage point, each field-block laid
+// out as value[3], jac[3][3], Lvalue[3], Ljac[3][3] (jac[c][j] = d_j a_c).
+// Output P: 3 fields (PW_F, PW_T) or 9 fields (PW_GT: A, B, Q).
+template <typename T>
+void pointwise(PwMode mode, const T* X, const T* C, T* P, long long vol, cudaStream_t st);
+
+// Semi-Lagrangian state step (Eq. 52): m_next(x) = m(X_n(x)), foot point from
+// v_next (at x) and v_cur (trilinear); also writes the displacement off[3].
+template <typename T>
+void transport_step(const T* m, const T* vnext, const T* vcur, T* mnext, T* off,
+                    Dims g, double dt, cudaStream_t st);
+// s = grad m . dv (central differences).
+template <typename T>
+void grad_dot(const T* m, const T* dv, T* s, Dims g, cudaStream_t st);
+// Incremental state step (Eq. 31) along the stored characteristic; dm may be
+// null (dm_0 = 0).
+template <typename T>
+void inc_step(const T* dm, const T* s, const T* mnext, const T* dvnext, const T* off,
+              T* dmnext, T* snext, Dims g, double dt, cudaStream_t st);
+// out_j = coef * r * d_j m, r = (m - y) if diff else y.
+template <typename T>
+void terminal_field(const T* m, const T* y, int diff, double coef, T* out, Dims g,
+                    cudaStream_t st);
+
+// ---- band vectors and reductions (grid.cu) --------------------------------
+template <typename T>
+void hermitianize(const cplx<T>* in, cplx<T>* out, int ncomp, Band b, cudaStream_t st);
+// out = a x + b y (complex arrays of n entries; y may be null).
+template <typename T>
+void axpby(cplx<T>* out, double a, const cplx<T>* x, double bcoef, const cplx<T>* y,
+           long long n, cudaStream_t st);
+// FP64 reductions written to a device double (deterministic two-pass tree).
+template <typename T>
+void sum_sq_diff(const T* a, const T* b, long long n, double* partial, double* out,
+                 cudaStream_t st);
+template <typename T>
+void inner_V(const cplx<T>* a, const cplx<T>* b, const T* Lhat, int ncomp, long long kvol,
+             double* partial, double* out, cudaStream_t st);
+constexpr int kReduceBlocks = 304;   // 2 x 152 SMs
+
+}  // namespace lddmm

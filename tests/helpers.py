@@ -1,0 +1,51 @@
+"""Shared helpers of the GPU parity tests (not a test module)."""
+
+import numpy as np
+
+from oracle import bl, objective
+from paper_1807_11560_gb300 import Context, inputs
+
+ALPHA, S, SIGMA = 0.0025, 2, 0.03
+
+
+def torch_dev(x, precision):
+    import torch
+    if np.iscomplexobj(x):
+        dt = torch.complex128 if precision == "fp64" else torch.complex64
+    else:
+        dt = torch.float64 if precision == "fp64" else torch.float32
+    return torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=dt).contiguous()
+
+
+def host(x):
+    return x.detach().cpu().numpy().astype(np.complex128 if x.is_complex() else np.float64)
+
+
+def quantise(x, precision):
+    """The values the GPU actually receives (so input rounding is not counted as error)."""
+    if precision == "fp64":
+        return np.asarray(x)
+    return np.asarray(x).astype(np.complex64 if np.iscomplexobj(x) else np.float32).astype(
+        np.complex128 if np.iscomplexobj(x) else np.float64)
+
+
+def rel_V(a, b, Ks):
+    L = bl.lhat(tuple(Ks), ALPHA, S)
+    return float(np.sqrt(np.sum(L * np.abs(a - b) ** 2) / np.sum(L * np.abs(b) ** 2)))
+
+
+def rel_2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(np.asarray(b).ravel()))
+
+
+def problem(kind, Ns, Ks, seed, Nt, precision, max_disp=2.0, v_disp=2.0, **ctx_kw):
+    """(Context with images set, oracle Problem on the same quantised images, v0, p)."""
+    I0, I1 = inputs.make_pair(kind, Ns, seed, max_disp=max_disp)
+    I0, I1 = quantise(I0, precision), quantise(I1, precision)
+    d = len(Ns)
+    v0 = quantise(inputs.random_bl(Ks, d, seed + 1, v_disp, Ns), precision)
+    p = quantise(inputs.random_bl(Ks, d, seed + 2, 1.0, Ns), precision)
+    ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision=precision, **ctx_kw)
+    ctx.set_images(torch_dev(I0, precision), torch_dev(I1, precision))
+    P = objective.Problem(I0, I1, Ks, ALPHA, S, SIGMA, Nt)
+    return ctx, P, v0, p
