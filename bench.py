@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 LDDMM library: GN Hessian-vector products per second.
+
+One step = one inexact Gauss-Newton-Krylov iteration of the hot path (gradient
+with forward shoot, transport and adjoint Jacobi sweep; 20 PCG iterations,
+each one GN Hessian-vector product; Armijo line search) on the 3D 64^3
+ellipsoid phantom, band 16^3, Nt = 10, FP32 with FP64 reductions.
+``value`` = Hessian-vector products per second over the timed steps, summed
+over ranks (each rank registers its own pair: weak scaling, no collective on
+the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+``--impl reference`` times the FP64 CPU oracle on the host cores (one
+Hessian-vector product per step at a fixed linearisation point).
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GN Hessian-vector products/sec and GN solve time at 1e-5 rel. error vs FP64 oracle"
+UNIT = "hessvec/s"
+ALPHA, S, SIGMA = 0.0025, 2, 0.03
+N_PCG = 20
+N_GN_CONFIG = 10
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="3d_64_ellipsoids")
+    ap.add_argument("--probe", default="inc_step", help="kernel class timed for the roofline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1807_11560_gb300 import inputs
+    kind, Ns, Ks, Nt, seed = inputs.WORKLOADS[name]
+    return kind, Ns, Ks, Nt, seed
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
+        flat = {}
+
+        def walk(d):
+            for k, v in d.items():
+                if isinstance(v, dict):
+                    walk(v)
+                elif isinstance(v, (int, float)):
+                    flat.setdefault(k, float(v))
+        walk(data)
+        if "hbm_gbs" in flat:
+            return flat, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.path = tempfile.mktemp(suffix=".csv")
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if device_uuid:
+            cmd[1:1] = ["-i", device_uuid]
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- oracle
+def oracle_hessvec_rate(name, n_hv, seed_offset=0):
+    """Hessian-vector products of the FP64 oracle per second (bounded sample)."""
+    import numpy as np
+    from oracle import objective
+    from paper_1807_11560_gb300 import inputs
+    kind, Ns, Ks, Nt, seed = workload(name)
+    I0, I1 = inputs.make_pair(kind, Ns, seed + seed_offset)
+    P = objective.Problem(I0, I1, Ks, ALPHA, S, SIGMA, Nt)
+    v0 = inputs.random_bl(Ks, len(Ns), seed + 1, 2.0, Ns)
+    lin = P.gradient(v0)
+    p = inputs.random_bl(Ks, len(Ns), seed + 2, 1.0, Ns)
+    times = []
+    for _ in range(n_hv):
+        t0 = time.perf_counter()
+        P.hessvec(lin, p)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    name = args.workload
+    kind, Ns, Ks, Nt, seed = workload(name)
+    times = oracle_hessvec_rate(name, args.warmup + args.steps)[args.warmup:]
+    total = sum(times)
+    value = len(times) / total
+    sample = (f"{len(times)} GN Hessian-vector products of the FP64 NumPy oracle at a fixed "
+              f"linearisation point ({name}), one per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": name, "grid": list(Ns), "band": list(Ks), "Nt": Nt, "pcg_per_gn": N_PCG,
+                   "l2": "oracle on host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host_cores": os.cpu_count()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+def algorithmic_work(cls, Ns, Ks, Nt):
+    """(bound, per-launch algorithmic amount, unit) of a probed kernel class."""
+    import numpy as np
+    nvox = int(np.prod(Ns))
+    if cls == "inc_step":
+        return "hbm", 12.0 * nvox, "B"          # read m_n, dm_n; write dm_{n+1}
+    if cls == "transport":
+        return "hbm", 8.0 * nvox, "B"           # read m_n; write m_{n+1}
+    raise ValueError(cls)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1807_11560_gb300 import Context, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    name = args.workload
+    kind, Ns, Ks, Nt, seed = workload(name)
+    d = len(Ns)
+    I0, I1 = inputs.make_pair(kind, Ns, seed + 1000 * rank)
+    I0d = torch.as_tensor(I0, dtype=torch.float32, device=dev)
+    I1d = torch.as_tensor(I1, dtype=torch.float32, device=dev)
+    ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision="fp32")
+    ctx.set_images(I0d, I1d)
+    v = torch.zeros((d,) + tuple(Ks), dtype=torch.complex64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ctx.probe(args.probe)
+
+    for _ in range(args.warmup):
+        ctx.gn_solve(v, 1, N_PCG)
+    ctx.probe_read()                                      # discard warm-up probe time
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = Clocks(uuid)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    hv = 0
+    k0 = ctx.kernel_count
+    barrier()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))                             # L2 flush between steps (untimed)
+        starts[k].record()
+        rep = ctx.gn_solve(v, 1, N_PCG)
+        ends[k].record()
+        hv += rep["pcg_iters"]
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    launches = ctx.kernel_count - k0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_dev = sum(step_ms) / 1e3
+    probe_ms, probe_n = ctx.probe_read()
+
+    tt = torch.tensor([t_dev, float(hv)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = tt.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tmax[1:2], op=dist.ReduceOp.SUM)
+        t_dev, hv_all = float(tmax[0]), float(tmax[1])
+    else:
+        hv_all = float(hv)
+    value = hv_all / t_dev
+
+    # pure Hessian-vector rate at a fixed linearisation point (context figure)
+    g = torch.empty_like(v)
+    ctx.gradient(v, g)
+    p = torch.as_tensor(inputs.random_bl(Ks, d, seed + 2, 1.0, Ns), dtype=torch.complex64, device=dev)
+    out = torch.empty_like(p)
+    for _ in range(3):
+        ctx.hessvec(p, out)
+    n_fix = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(n_fix):
+        ctx.hessvec(p, out)
+    e1.record()
+    torch.cuda.synchronize()
+    hv_fixed = n_fix / (e0.elapsed_time(e1) / 1e3)
+
+    # end to end through the C interface with host buffers
+    I0h = torch.as_tensor(I0, dtype=torch.float32).pin_memory()
+    I1h = torch.as_tensor(I1, dtype=torch.float32).pin_memory()
+    vh = torch.zeros((d,) + tuple(Ks), dtype=torch.complex64).pin_memory()
+    vh.copy_(v.cpu())
+    hv_e2e = 0
+    barrier()
+    te0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.set_images(I0h, I1h)
+        rep = ctx.gn_solve(vh, 1, N_PCG)
+        hv_e2e += rep["pcg_iters"]
+    barrier()
+    te = time.perf_counter() - te0
+    if world > 1:
+        tt = torch.tensor([te, float(hv_e2e)], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:2], op=dist.ReduceOp.SUM)
+        te, hv_e2e = float(tt[0]), float(tt[1])
+    e2e_value = hv_e2e / te
+
+    if rank == 0:
+        peaks, src = load_peaks()
+        bound, work, wunit = algorithmic_work(args.probe, Ns, Ks, Nt)
+        avg_s = (probe_ms / 1e3) / max(probe_n, 1)
+        if bound == "hbm":
+            achieved = work / avg_s / 1e9
+            peak = peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+            runit = "GB/s"
+        roof = {"bound": bound, "kernel": args.probe, "achieved": achieved, "peak": peak, "unit": runit,
+                "frac": achieved / peak, "traffic": None, "peak_source": f"{src} (of {src})",
+                "launches_timed": probe_n, "avg_launch_us": avg_s * 1e6,
+                "algorithmic_per_launch": work, "algorithmic_unit": wunit}
+        cpu = None
+        if not args.no_cpu_baseline:
+            times = oracle_hessvec_rate(name, 3)
+            cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{len(times)} GN Hessian-vector products of the FP64 NumPy oracle on {name} "
+                             "at a fixed linearisation point (single-threaded numpy/pocketfft)",
+                   "host_cores": os.cpu_count()}
+        nvox, nband = int(np.prod(Ns)), d * int(np.prod(Ks))
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": name, "grid": list(Ns), "band": list(Ks), "Nt": Nt,
+                       "pcg_per_gn": N_PCG, "step": "one GN iteration (gradient, 20 PCG Hessvecs, Armijo)",
+                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "gn_solve_s": 1e-3 * statistics.mean(step_ms) * N_GN_CONFIG,
+            "gn_solve_note": f"{N_GN_CONFIG} GN x {N_PCG} PCG at the mean timed step time",
+            "hessvec_per_s_fixed_point": hv_fixed,
+            "wall_s": t_wall,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": 2 * nvox * 4 + nband * 8, "d2h_bytes_per_step": nband * 8},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

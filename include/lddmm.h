@@ -178,6 +178,21 @@ int lddmm_transport(lddmm_ctx* ctx, const void* v0, void* m1_out);
 /* dm(1) of the last lddmm_hessvec call (incremental state, Eq. 31). */
 int lddmm_last_dm1(lddmm_ctx* ctx, void* dm1_out);
 
+/* Timing probe.  Brackets every launch of one kernel class with CUDA events
+ * on the stream it runs on (also inside the captured Hessian-vector graph)
+ * and accumulates the elapsed device time.  kernel_class is one of
+ * "transport" (state step, Eq. 52), "inc_step" (incremental state step,
+ * Eq. 31), "pointwise" (bracket products), "iota_pad" / "pi_pad" (transforms
+ * on the padded product grid), "iota_full" / "pi_full" (transforms on the
+ * image grid); NULL or "" switches the probe off.  Changing the class
+ * rebuilds the graph on the next product.  Not part of the method; the
+ * paper has no counterpart. */
+int lddmm_probe(lddmm_ctx* ctx, const char* kernel_class);
+
+/* Accumulated probe time (ms) and number of timed launches since the last
+ * read or lddmm_probe call; resets both. */
+int lddmm_probe_read(lddmm_ctx* ctx, double* total_ms, long long* launches);
+
 /* Number of CUDA kernels this context has launched since creation (graph
  * replays count each kernel node). */
 long long lddmm_kernel_count(const lddmm_ctx* ctx);

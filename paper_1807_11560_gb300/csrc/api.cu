@@ -41,6 +41,11 @@ struct Fail {
   int code;
 };
 
+enum ProbeClass { PR_TRANSPORT = 0, PR_INC, PR_POINTWISE, PR_IOTA_PAD, PR_PI_PAD, PR_IOTA_FULL,
+                  PR_PI_FULL, PR_COUNT };
+const char* const kProbeNames[PR_COUNT] = {"transport", "inc_step", "pointwise", "iota_pad",
+                                           "pi_pad", "iota_full", "pi_full"};
+
 template <typename T>
 struct State {
   cplx<T>* vh = nullptr;    // [Nt+1][3][Kvol]
@@ -86,6 +91,19 @@ struct Impl {
   long long hv_nodes = 0;
   cudaStream_t cap = nullptr;
   cudaEvent_t ev = nullptr;
+  bool capturing = false;
+  // kernel-class probe: CUDA events around every launch of one class, read
+  // back after each stream synchronisation (also inside the captured graph,
+  // as external event-record nodes)
+  int probe = -1;
+  std::vector<cudaEvent_t> evpool;
+  size_t evnext = 0;
+  cudaEvent_t pstart = nullptr;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend_direct, graph_pairs;
+  std::vector<cudaEvent_t> graph_events;
+  bool graph_pending = false;
+  double probe_ms = 0.0;
+  long long probe_n = 0;
 
   // ---------------------------------------------------------------- utils
   void cuda(cudaError_t e, const char* what) {
@@ -115,6 +133,10 @@ struct Impl {
     cap = nullptr;
     if (ev) cudaEventDestroy(ev);
     ev = nullptr;
+    for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+    evpool.clear();
+    for (cudaEvent_t e : graph_events) cudaEventDestroy(e);
+    graph_events.clear();
     for (void* q : allocs) cudaFree(q);
     allocs.clear();
     if (hres) cudaFreeHost(hres);
@@ -250,7 +272,58 @@ struct Impl {
     cuda(cudaMemcpyAsync(user, src, (size_t)duser * Kvol * sizeof(C), cudaMemcpyDefault, st),
          "copy BL output");
   }
-  void sync(const char* what) { cuda(cudaStreamSynchronize(st), what); }
+  void sync(const char* what) {
+    cuda(cudaStreamSynchronize(st), what);
+    collect();
+  }
+
+  // ------------------------------------------------------------- probe
+  cudaEvent_t probe_event() {
+    cudaEvent_t e = nullptr;
+    if (capturing) {
+      cuda(cudaEventCreate(&e), "probe event");
+      graph_events.push_back(e);
+      return e;
+    }
+    if (evnext == evpool.size()) {
+      cuda(cudaEventCreate(&e), "probe event");
+      evpool.push_back(e);
+    }
+    return evpool[evnext++];
+  }
+  void probe_record(cudaEvent_t e) {
+    cuda(cudaEventRecordWithFlags(e, st, capturing ? cudaEventRecordExternal : cudaEventRecordDefault),
+         "probe record");
+  }
+  void pb(int cls) {
+    if (cls != probe) return;
+    pstart = probe_event();
+    probe_record(pstart);
+  }
+  void pe(int cls) {
+    if (cls != probe) return;
+    cudaEvent_t e = probe_event();
+    probe_record(e);
+    (capturing ? graph_pairs : pend_direct).push_back({pstart, e});
+  }
+  void collect() {
+    float ms = 0.f;
+    for (auto& pr : pend_direct) {
+      cuda(cudaEventElapsedTime(&ms, pr.first, pr.second), "probe elapsed");
+      probe_ms += ms;
+      ++probe_n;
+    }
+    pend_direct.clear();
+    evnext = 0;
+    if (graph_pending) {
+      for (auto& pr : graph_pairs) {
+        cuda(cudaEventElapsedTime(&ms, pr.first, pr.second), "probe elapsed");
+        probe_ms += ms;
+        ++probe_n;
+      }
+      graph_pending = false;
+    }
+  }
 
   // -------------------------------------------------------- descriptors
   IotaDesc<T> block24(const C* srcA, const C* srcB, T* dst) const {
@@ -299,12 +372,18 @@ struct Impl {
   // one evaluation of a bracket expression at a Heun stage point
   void eval(PwMode mode, T* slot, const C* srcA, const C* srcB, const PiEpi<T>& e) {
     T* dst = (mode == PW_F) ? slot : X;
+    pb(PR_IOTA_PAD);
     iota_batch<T>(pad, block24(srcA, srcB, dst), Lhat, T1, T2, st);
+    pe(PR_IOTA_PAD);
+    pb(PR_POINTWISE);
     pointwise<T>(mode, X, slot, P, Mvol, st);
+    pe(PR_POINTWISE);
     PiSrc<T> ps{};
     ps.nf = (mode == PW_GT) ? 9 : 3;
     for (int f = 0; f < ps.nf; ++f) ps.src[f] = P + f * Mvol;
+    pb(PR_PI_PAD);
     pi_batch<T>(pad, ps, e, Lhat, T1, T2, st);
+    pe(PR_PI_PAD);
     launches += kIotaLaunches + 1 + kPiLaunches;
     check_launch("bracket evaluation");
   }
@@ -323,7 +402,9 @@ struct Impl {
           d.deriv[f] = -1;
           d.applyL[f] = 0;
         }
+      pb(PR_IOTA_FULL);
       iota_batch<T>(full, d, Lhat, T1, T2, st);
+      pe(PR_IOTA_FULL);
       launches += kIotaLaunches;
     }
     check_launch("iota to image grid");
@@ -339,7 +420,9 @@ struct Impl {
     e.coef[0] = (T)(1.0 / (double)Nvol);
     e.applyK[0] = 1;
     add_out(e, out, 0, 1.0, {});
+    pb(PR_PI_FULL);
     pi_batch<T>(full, ps, e, Lhat, T1, T2, st);
+    pe(PR_PI_FULL);
     launches += kPiLaunches;
     check_launch("projection");
   }
@@ -375,10 +458,13 @@ struct Impl {
   void transport(State<T>& S) {
     to_grid(S.vh, Nt + 1, S.vgrid);
     cuda(cudaMemcpyAsync(S.mh, I0, (size_t)Nvol * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy I0");
-    for (int n = 0; n < Nt; ++n)
+    for (int n = 0; n < Nt; ++n) {
+      pb(PR_TRANSPORT);
       transport_step<T>(S.mh + n * Nvol, S.vgrid + (long long)(n + 1) * 3 * Nvol,
                         S.vgrid + (long long)n * 3 * Nvol, S.mh + (n + 1) * Nvol,
                         S.off + (long long)n * 3 * Nvol, N, dt, st);
+      pe(PR_TRANSPORT);
+    }
     launches += Nt;
     check_launch("transport");
   }
@@ -463,9 +549,11 @@ struct Impl {
     grad_dot<T>(S.mh, dvgrid, sb[0], N, st);
     ++launches;
     for (int n = 0; n < Nt; ++n) {
+      pb(PR_INC);
       inc_step<T>(n == 0 ? nullptr : dm[n & 1], sb[n & 1], S.mh + (long long)(n + 1) * Nvol,
                   dvgrid + (long long)(n + 1) * 3 * Nvol, S.off + (long long)n * 3 * Nvol,
                   dm[(n + 1) & 1], sb[(n + 1) & 1], N, dt, st);
+      pe(PR_INC);
     }
     launches += Nt;
     terminal_field<T>(S.mh + (long long)Nt * Nvol, dm[Nt & 1], 0, -2.0 / (sigma * sigma), fterm, N, st);
@@ -545,6 +633,18 @@ struct Impl {
       cudaGraphExecDestroy(hv_exec);
       hv_exec = nullptr;
     }
+    for (cudaEvent_t e : graph_events) cudaEventDestroy(e);
+    graph_events.clear();
+    graph_pairs.clear();
+    graph_pending = false;
+  }
+
+  void set_probe(int cls) {
+    sync("probe");
+    if (cls != probe) invalidate_graph();
+    probe = cls;
+    probe_ms = 0.0;
+    probe_n = 0;
   }
 
   // Hessian-vector product with input already in dvh[0]; result in vout
@@ -558,6 +658,7 @@ struct Impl {
       cuda(cudaEventRecord(ev, st), "event record");
       cuda(cudaStreamWaitEvent(cap, ev, 0), "wait");
       cuda(cudaGraphLaunch(hv_exec, cap), "graph launch");
+      graph_pending = !graph_pairs.empty();
       cuda(cudaEventRecord(ev, cap), "event record");
       cuda(cudaStreamWaitEvent(st, ev, 0), "wait");
       launches += hv_nodes;
@@ -573,14 +674,17 @@ struct Impl {
     const long long before = launches;
     cudaGraph_t g = nullptr;
     cuda(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    capturing = true;
     try {
       enqueue_hessvec();
     } catch (...) {
+      capturing = false;
       cudaStreamEndCapture(cap, &g);
       if (g) cudaGraphDestroy(g);
       st = user;
       throw;
     }
+    capturing = false;
     st = user;
     cuda(cudaStreamEndCapture(cap, &g), "end capture");
     hv_nodes = launches - before;
@@ -955,6 +1059,32 @@ int lddmm_last_dm1(lddmm_ctx* ctx, void* out) {
   if (!ctx) return LDDMM_EINVAL;
   if (bad_ptr(ctx, out, "dm1_out")) return LDDMM_EINVAL;
   return lddmm::dispatch(ctx, [&](auto& im) { im.last_dm1(out); });
+}
+
+int lddmm_probe(lddmm_ctx* ctx, const char* kernel_class) {
+  if (!ctx) return LDDMM_EINVAL;
+  int cls = -1;
+  if (kernel_class && kernel_class[0]) {
+    for (int i = 0; i < lddmm::PR_COUNT; ++i)
+      if (std::strcmp(kernel_class, lddmm::kProbeNames[i]) == 0) cls = i;
+    if (cls < 0) {
+      ctx->err = std::string("unknown kernel class: ") + kernel_class;
+      return LDDMM_EINVAL;
+    }
+  }
+  return lddmm::dispatch(ctx, [&](auto& im) { im.set_probe(cls); });
+}
+
+int lddmm_probe_read(lddmm_ctx* ctx, double* total_ms, long long* launches) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, total_ms, "total_ms") || bad_ptr(ctx, launches, "launches")) return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) {
+    im.sync("probe read");
+    *total_ms = im.probe_ms;
+    *launches = im.probe_n;
+    im.probe_ms = 0.0;
+    im.probe_n = 0;
+  });
 }
 
 long long lddmm_kernel_count(const lddmm_ctx* ctx) {

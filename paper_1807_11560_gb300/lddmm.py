@@ -69,6 +69,8 @@ def lib():
         "lddmm_transport": (I, [P, P, P]),
         "lddmm_last_dm1": (I, [P, P]),
         "lddmm_kernel_count": (ctypes.c_longlong, [P]),
+        "lddmm_probe": (I, [P, ctypes.c_char_p]),
+        "lddmm_probe_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]),
         "lddmm_last_error": (ctypes.c_char_p, [P]),
         "lddmm_destroy": (None, [P]),
     }
@@ -230,6 +232,16 @@ class Context:
 
     def last_dm1(self, out):
         self._check(lib().lddmm_last_dm1(self._h, self._arg(out, "real", self.nvox)))
+
+    def probe(self, kernel_class):
+        """Time every launch of one kernel class with CUDA events (None: off)."""
+        self._check(lib().lddmm_probe(self._h, (kernel_class or "").encode()))
+
+    def probe_read(self):
+        """(total device ms, timed launches) since the last read."""
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        self._check(lib().lddmm_probe_read(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     @property
     def kernel_count(self):
