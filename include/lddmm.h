@@ -157,6 +157,36 @@ int lddmm_gn_solve(lddmm_ctx* ctx, void* v0_inout, int n_gn, int n_pcg, lddmm_re
  * values [ncomp][N..] on the image grid. */
 int lddmm_iota(lddmm_ctx* ctx, const void* a, int ncomp, void* f_out);
 
+/* Allocation-free iota for callers that cannot let a library allocate
+ * device memory: a host framework whose caching allocator already holds
+ * nearly all device memory, a latency-bound loop that cannot absorb the
+ * device-wide synchronisation cudaFree implies, or a plugin host that forbids
+ * libraries from allocating.  The paper has no counterpart; this is the same
+ * transform as lddmm_iota on an FP32 context, without a context.
+ *   ndim, grid, K  as in lddmm_create (host int arrays).
+ *   a              device pointer, complex64 [ncomp][K..], symmetrised on entry.
+ *   ncomp          1..36 scalar fields.
+ *   f_out          device pointer, float32 [ncomp][N..].
+ *   stream         cudaStream_t (NULL = legacy default stream).
+ * The call is asynchronous: it returns once its kernels are enqueued.
+ * It calls no cudaMalloc or cudaFree.  Its scratch is one fixed 32 MiB
+ * static device array that every GPU loading this library holds until the
+ * process exits.  A problem needs, each rounded up to 256 bytes, the twiddle
+ * tables (K3 N3 + K2 N2 + K1/2 N1 complex64 values), the symmetrised input
+ * (ncomp K1 K2 K3) and two intermediates (ncomp K1/2 K2 N3 and
+ * ncomp K1/2 N2 N3); if that exceeds 32 MiB the call returns LDDMM_ENOMEM and
+ * does nothing (3 fields on 160x192x160 with band 32^3 need about 14 MiB).
+ * LDDMM_EINVAL for bad sizes or for a or f_out not being device memory.
+ * The first call on each device performs a one-time set-up (it looks up the
+ * device address of the scratch array); make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last
+ * call's contents; every call rewrites everything it reads, so nothing has
+ * to start at zero.  Calls that overlap on the GPU (on different streams, or
+ * from several host threads on one device) race on the array: serialise
+ * them. */
+int lddmm_iota_noalloc(int ndim, const int* grid, const int* K, const void* a, int ncomp,
+                       void* f_out, void* stream);
+
 /* pi: ncomp grid fields [ncomp][N..] -> band coefficients [ncomp][K..]. */
 int lddmm_pi(lddmm_ctx* ctx, const void* f, int ncomp, void* a_out);
 

@@ -71,6 +71,7 @@ def lib():
         "lddmm_kernel_count": (ctypes.c_longlong, [P]),
         "lddmm_probe": (I, [P, ctypes.c_char_p]),
         "lddmm_probe_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]),
+        "lddmm_iota_noalloc": (I, [I, ctypes.POINTER(I), ctypes.POINTER(I), P, I, P, P]),
         "lddmm_last_error": (ctypes.c_char_p, [P]),
         "lddmm_destroy": (None, [P]),
     }
@@ -97,6 +98,17 @@ def _ptr(x):
 
 def _dtype_name(x):
     return str(x.dtype).replace("torch.", "")
+
+
+def iota_noalloc(grid, K, a, ncomp, out, stream=None):
+    """lddmm_iota_noalloc: iota of ncomp band-limited scalar fields without any
+    device allocation (FP32; a and out must be CUDA tensors).  Asynchronous on
+    ``stream``; returns the status code (0 = OK)."""
+    grid, K = tuple(int(g) for g in grid), tuple(int(k) for k in K)
+    if _dtype_name(a) != "complex64" or _dtype_name(out) != "float32":
+        raise TypeError("iota_noalloc takes complex64 input and float32 output")
+    arr = ctypes.c_int * len(grid)
+    return lib().lddmm_iota_noalloc(len(grid), arr(*grid), arr(*K), _ptr(a), int(ncomp), _ptr(out), stream)
 
 
 class Context:

@@ -1,0 +1,63 @@
+"""The allocation-free transform entry point, lddmm_iota_noalloc.
+
+It serves callers that cannot let a library allocate device memory (a host
+framework whose allocator owns the device memory, latency-bound loops that
+cannot absorb cudaFree's synchronisation, plugin hosts that forbid it).  It
+must give the same grid values as the context-based lddmm_iota, call after
+call, although every call reuses one fixed scratch array.
+
+This file is collected last on purpose; it must pass on its own in a fresh
+process and after every other test.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1807_11560_gb300 import Context, inputs, lddmm
+
+pytestmark = pytest.mark.gpu
+
+ALPHA, S, SIGMA = 0.0025, 2, 0.03
+TOL = 2e-6            # the FP32 transform tolerance of the other GPU tests
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+@pytest.mark.parametrize("Ns,Ks", [((64, 64, 64), (16, 16, 16)), ((33, 17), (10, 6))])
+def test_noalloc_iota_matches_context_iota_on_two_calls(Ns, Ks):
+    import torch
+    d = len(Ns)
+    stream = torch.cuda.current_stream().cuda_stream
+    with Context(Ns, Ks, ALPHA, S, SIGMA, 2, precision="fp32") as ctx:
+        for seed in (3, 4):           # two calls in a row, different inputs
+            a = torch.as_tensor(inputs.random_bl(Ks, d, seed, 2.0, Ns), dtype=torch.complex64,
+                                device="cuda")
+            ref = torch.empty((d,) + Ns, dtype=torch.float32, device="cuda")
+            ctx.iota(a, d, ref)
+            out = torch.full((d,) + Ns, float("nan"), dtype=torch.float32, device="cuda")
+            rc = lddmm.iota_noalloc(Ns, Ks, a, d, out, stream)
+            assert rc == 0
+            torch.cuda.synchronize()
+            assert _rel(out.cpu().numpy(), ref.cpu().numpy()) < TOL
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch_and_host_pointers():
+    import torch
+    L = lddmm.lib()
+    arr = ctypes.c_int * 3
+    a = torch.zeros(8, dtype=torch.complex64, device="cuda")
+    f = torch.zeros(8, dtype=torch.float32, device="cuda")
+    # 36 fields on 512^3 with band 64^3 need far more than the fixed scratch
+    assert L.lddmm_iota_noalloc(3, arr(512, 512, 512), arr(64, 64, 64), a.data_ptr(), 36,
+                                f.data_ptr(), None) == 2        # LDDMM_ENOMEM
+    # an odd band is an argument error
+    assert L.lddmm_iota_noalloc(3, arr(16, 16, 16), arr(7, 8, 8), a.data_ptr(), 1,
+                                f.data_ptr(), None) == 1        # LDDMM_EINVAL
+    host = np.zeros(4 * 4 * 4, np.complex64)
+    out = torch.zeros((4, 4, 4), dtype=torch.float32, device="cuda")
+    assert L.lddmm_iota_noalloc(3, arr(4, 4, 4), arr(2, 2, 2), host.ctypes.data, 1,
+                                out.data_ptr(), None) == 1      # host input refused
