@@ -107,14 +107,16 @@ void lddmm_default_opts(lddmm_opts* opts);
 /* Create a registration context (Section 3.2).
  *   ndim    2 or 3.
  *   grid    ndim image sizes N_j >= 2 (int array, host).
- *   K       ndim band sizes: even, 2 <= K_j <= N_j (int array, host).
+ *   K       ndim band sizes: even, 2 <= K_j <= min(N_j, 512) (int array, host).
  *   alpha   > 0, s >= 1: L = (Id - alpha Lap)^s (Eq. 1).
  *   sigma   > 0: data weight 1/sigma^2 (Eq. 50).
  *   Nt      >= 1 time steps on [0,1].
  *   opts    NULL for defaults.
  * Allocates every device buffer the context needs (histories for Nt steps,
  * padded-grid caches, transform scratch).  Returns LDDMM_ENOMEM if the
- * device lacks memory, LDDMM_EINVAL for bad sizes.  *out is NULL on failure. */
+ * device lacks memory, LDDMM_EINVAL for bad sizes (including N_3 > 1024 and
+ * grids whose transform tiles exceed shared memory: N_3 above about 700 at
+ * K = 32 in FP32, half that in FP64).  *out is NULL on failure. */
 int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K,
                  double alpha, int s, double sigma, int Nt, const lddmm_opts* opts);
 
@@ -173,10 +175,10 @@ int lddmm_iota(lddmm_ctx* ctx, const void* a, int ncomp, void* f_out);
  * static device array that every GPU loading this library holds until the
  * process exits.  A problem needs, each rounded up to 256 bytes, the twiddle
  * tables (K3 N3 + K2 N2 + K1/2 N1 complex64 values), the symmetrised input
- * (ncomp K1 K2 K3) and two intermediates (ncomp K1/2 K2 N3 and
- * ncomp K1/2 N2 N3); if that exceeds 32 MiB the call returns LDDMM_ENOMEM and
- * does nothing (3 fields on 160x192x160 with band 32^3 need about 14 MiB).
- * LDDMM_EINVAL for bad sizes or for a or f_out not being device memory.
+ * (ncomp K1 K2 K3) and one intermediate (ncomp K1/2 N2 N3); if that exceeds
+ * 32 MiB the call returns LDDMM_ENOMEM and does nothing (3 fields on
+ * 160x192x160 with band 32^3 need about 13 MiB).  LDDMM_EINVAL for bad sizes
+ * (as in lddmm_create) or for a or f_out not being device memory.
  * The first call on each device performs a one-time set-up (it looks up the
  * device address of the scratch array); make that first call before any
  * stream capture.  All calls share the one array and it keeps the last
@@ -212,9 +214,9 @@ int lddmm_last_dm1(lddmm_ctx* ctx, void* dm1_out);
  * on the stream it runs on (also inside the captured Hessian-vector graph)
  * and accumulates the elapsed device time.  kernel_class is one of
  * "transport" (state step, Eq. 52), "inc_step" (incremental state step,
- * Eq. 31), "pointwise" (bracket products), "iota_pad" / "pi_pad" (transforms
- * on the padded product grid), "iota_full" / "pi_full" (transforms on the
- * image grid); NULL or "" switches the probe off.  Changing the class
+ * Eq. 31), "bracket" (one bracket evaluation of ad~* / ad~ on the padded
+ * product grid: its three kernels), "iota_full" / "pi_full" (transforms on
+ * the image grid); NULL or "" switches the probe off.  Changing the class
  * rebuilds the graph on the next product.  Not part of the method; the
  * paper has no counterpart. */
 int lddmm_probe(lddmm_ctx* ctx, const char* kernel_class);

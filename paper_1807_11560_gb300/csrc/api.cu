@@ -41,10 +41,9 @@ struct Fail {
   int code;
 };
 
-enum ProbeClass { PR_TRANSPORT = 0, PR_INC, PR_POINTWISE, PR_IOTA_PAD, PR_PI_PAD, PR_IOTA_FULL,
-                  PR_PI_FULL, PR_COUNT };
-const char* const kProbeNames[PR_COUNT] = {"transport", "inc_step", "pointwise", "iota_pad",
-                                           "pi_pad", "iota_full", "pi_full"};
+enum ProbeClass { PR_TRANSPORT = 0, PR_INC, PR_BRACKET, PR_IOTA_FULL, PR_PI_FULL, PR_COUNT };
+const char* const kProbeNames[PR_COUNT] = {"transport", "inc_step", "bracket", "iota_full",
+                                           "pi_full"};
 
 template <typename T>
 struct State {
@@ -73,8 +72,7 @@ struct Impl {
   T *I0 = nullptr, *I1 = nullptr;
   State<T> lin, trial;
   bool have_images = false, have_lin = false, have_dm1 = false;
-  C *T1 = nullptr, *T2 = nullptr;
-  T *X = nullptr, *P = nullptr;
+  C *T2 = nullptr, *P2 = nullptr;
   C *k1 = nullptr, *aU = nullptr, *aW = nullptr, *Ut = nullptr, *Wt = nullptr, *U = nullptr,
     *W = nullptr, *dstar = nullptr, *vin = nullptr, *vout = nullptr, *gbuf = nullptr;
   C *px = nullptr, *pr = nullptr, *pd = nullptr, *pq = nullptr, *vsol = nullptr, *vtry = nullptr;
@@ -218,6 +216,10 @@ struct Impl {
 
     make_plan(full, N);
     make_plan(pad, M);
+    if (max_smem_needed<T>(full, 1, false) > smem_limit() || max_smem_needed<T>(pad, 3, true) > smem_limit()) {
+      *err = "grid or band too large for the transform tiles (N_3 <= 1024, shared memory)";
+      throw Fail{LDDMM_EINVAL};
+    }
     std::vector<T> L((size_t)Kvol);
     for (int q1 = 0; q1 < K.k1; ++q1)
       for (int q2 = 0; q2 < K.k2; ++q2)
@@ -234,12 +236,9 @@ struct Impl {
     make_state(lin);
     make_state(trial);
     const long long H1 = K.h1;
-    const long long t1 = std::max(33LL * H1 * K.k2 * N.n3, 24LL * H1 * K.k2 * M.n3);
     const long long t2 = std::max(33LL * H1 * N.n2 * N.n3, 24LL * H1 * M.n2 * M.n3);
-    alloc(T1, (size_t)t1);
     alloc(T2, (size_t)t2);
-    alloc(X, (size_t)24 * Mvol);
-    alloc(P, (size_t)9 * Mvol);
+    alloc(P2, (size_t)9 * H1 * M.n2 * M.n3);
     for (C** b : {&k1, &aU, &aW, &Ut, &Wt, &U, &W, &dstar, &vin, &vout, &gbuf, &px, &pr, &pd, &pq,
                   &vsol, &vtry})
       alloc(*b, (size_t)3 * Kvol);
@@ -371,20 +370,10 @@ struct Impl {
 
   // one evaluation of a bracket expression at a Heun stage point
   void eval(PwMode mode, T* slot, const C* srcA, const C* srcB, const PiEpi<T>& e) {
-    T* dst = (mode == PW_F) ? slot : X;
-    pb(PR_IOTA_PAD);
-    iota_batch<T>(pad, block24(srcA, srcB, dst), Lhat, T1, T2, st);
-    pe(PR_IOTA_PAD);
-    pb(PR_POINTWISE);
-    pointwise<T>(mode, X, slot, P, Mvol, st);
-    pe(PR_POINTWISE);
-    PiSrc<T> ps{};
-    ps.nf = (mode == PW_GT) ? 9 : 3;
-    for (int f = 0; f < ps.nf; ++f) ps.src[f] = P + f * Mvol;
-    pb(PR_PI_PAD);
-    pi_batch<T>(pad, ps, e, Lhat, T1, T2, st);
-    pe(PR_PI_PAD);
-    launches += kIotaLaunches + 1 + kPiLaunches;
+    pb(PR_BRACKET);
+    bracket_eval<T>(pad, mode, block24(srcA, srcB, slot), slot, e, Lhat, T2, P2, st);
+    pe(PR_BRACKET);
+    launches += kBracketLaunches;
     check_launch("bracket evaluation");
   }
 
@@ -403,7 +392,7 @@ struct Impl {
           d.applyL[f] = 0;
         }
       pb(PR_IOTA_FULL);
-      iota_batch<T>(full, d, Lhat, T1, T2, st);
+      iota_batch<T>(full, d, Lhat, T2, st);
       pe(PR_IOTA_FULL);
       launches += kIotaLaunches;
     }
@@ -421,7 +410,7 @@ struct Impl {
     e.applyK[0] = 1;
     add_out(e, out, 0, 1.0, {});
     pb(PR_PI_FULL);
-    pi_batch<T>(full, ps, e, Lhat, T1, T2, st);
+    pi_batch<T>(full, ps, e, Lhat, T2, st);
     pe(PR_PI_FULL);
     launches += kPiLaunches;
     check_launch("projection");
@@ -801,7 +790,7 @@ struct Impl {
         d.deriv[c] = -1;
         d.applyL[c] = 0;
       }
-      iota_batch<T>(full, d, Lhat, T1, T2, st);
+      iota_batch<T>(full, d, Lhat, T2, st);
       launches += kIotaLaunches;
       check_launch("iota");
       cuda(cudaMemcpyAsync((T*)out + (long long)c0 * Nvol, fterm, (size_t)nc * Nvol * sizeof(T),
@@ -823,7 +812,7 @@ struct Impl {
       e.coef[0] = (T)(1.0 / (double)Nvol);
       e.applyK[0] = 0;
       add_out(e, vout, 0, 1.0, {});
-      pi_batch<T>(full, ps, e, Lhat, T1, T2, st);
+      pi_batch<T>(full, ps, e, Lhat, T2, st);
       launches += kPiLaunches;
       check_launch("pi");
       cuda(cudaMemcpyAsync((C*)out + (long long)c0 * Kvol, vout, (size_t)nc * Kvol * sizeof(C),
@@ -840,7 +829,7 @@ struct Impl {
     e.coef[0] = (T)(1.0 / (double)Mvol);
     e.applyK[0] = 1;
     add_out(e, vout, 0, 1.0, {});
-    eval(PW_F, X, px, pr, e);       // P(v, L u) with v-fields from px, L-fields from pr
+    eval(PW_F, slot(trial, 0), px, pr, e);   // P(v, L u): v-fields from px, L-fields from pr
     store_bl(vout, out);
     sync("ad_dagger");
   }
@@ -849,20 +838,13 @@ struct Impl {
     load_bl(v, px);
     load_bl(w, pr);
     T* vslot = slot(trial, 0);
-    iota_batch<T>(pad, block24(px, px, vslot), Lhat, T1, T2, st);
-    iota_batch<T>(pad, block24(pr, pr, X), Lhat, T1, T2, st);
-    pointwise<T>(PW_GT, X, vslot, P, Mvol, st);
-    PiSrc<T> ps{};
-    ps.nf = 3;
-    for (int c = 0; c < 3; ++c) ps.src[c] = P + (6 + c) * Mvol;
-    PiEpi<T> e = epi(3, 1);
-    e.grp[0] = 0;
-    e.coef[0] = (T)(1.0 / (double)Mvol);
-    e.applyK[0] = 0;
+    eval(PW_F, vslot, px, px, epi(3, 1));          // caches the fields of v; no output
+    PiEpi<T> e = epi(3, 3);                          // keep only Q(v, w) = Dv w - Dw v
+    e.grp[0] = 0; e.coef[0] = (T)0;
+    e.grp[1] = 0; e.coef[1] = (T)0;
+    e.grp[2] = 0; e.coef[2] = (T)(1.0 / (double)Mvol);
     add_out(e, vout, 0, 1.0, {});
-    pi_batch<T>(pad, ps, e, Lhat, T1, T2, st);
-    launches += 2 * kIotaLaunches + 1 + kPiLaunches;
-    check_launch("ad");
+    eval(PW_GT, vslot, pr, pr, e);
     store_bl(vout, out);
     sync("ad");
   }
@@ -949,7 +931,7 @@ int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, doubl
   if ((ndim != 2 && ndim != 3) || !grid || !K || !(alpha > 0) || s < 1 || !(sigma > 0) || Nt < 1)
     return LDDMM_EINVAL;
   for (int j = 0; j < ndim; ++j) {
-    if (grid[j] < 2 || K[j] < 2 || (K[j] & 1) || K[j] > grid[j] || grid[j] > (1 << 16))
+    if (grid[j] < 2 || K[j] < 2 || (K[j] & 1) || K[j] > grid[j] || grid[j] > (1 << 16) || K[j] > 512)
       return LDDMM_EINVAL;
   }
   lddmm_opts o;

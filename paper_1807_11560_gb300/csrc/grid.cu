@@ -1,5 +1,4 @@
 // Grid-point kernels of the GB300 LDDMM library (sm_103a):
-//   * bracket products of ad~* and ad~ on the padded grid (Eqs. 4, 48, 49),
 //   * semi-Lagrangian state and incremental-state transport on the image grid
 //     (Eqs. 52 and 31),
 //   * terminal adjoint fields lambda(1) grad m(1) (Eq. 55, Eq. 58 under GN),
@@ -15,75 +14,6 @@ constexpr int kThreads = 256;
 inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 __device__ __forceinline__ bool nyq(int q, int K) { return (K % 2 == 0) && (2 * q == K); }
-
-// ---- bracket products --------------------------------------------------------
-// Field block layout: a[c] at c, Da[c][j] = d_j a_c at 3 + 3c + j.
-// P(a, m)_i = sum_j Da[j][i] m_j + sum_j Dm[i][j] a_j + m_i div a   (ad* bracket, Eq. 4)
-// Q(a, w)_i = sum_j Da[i][j] w_j - Dw[i][j] a_j                      (ad bracket, Eq. 49)
-template <typename T>
-__device__ __forceinline__ void bracketP(const T* a, const T* m, T* out) {
-  const T* Da = a + 3;
-  const T* Dm = m + 3;
-  const T div = Da[0] + Da[4] + Da[8];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    T s = m[i] * div;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) s = fma(Da[3 * j + i], m[j], fma(Dm[3 * i + j], a[j], s));
-    out[i] += s;
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void bracketQ(const T* a, const T* w, T* out) {
-  const T* Da = a + 3;
-  const T* Dw = w + 3;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    T s = T(0);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) s = fma(Da[3 * i + j], w[j], fma(-Dw[3 * i + j], a[j], s));
-    out[i] += s;
-  }
-}
-
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreads)
-k_pointwise(const T* __restrict__ X, const T* __restrict__ Cc, T* __restrict__ P, long long vol) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= vol) return;
-  T cv[12], cl[12];
-#pragma unroll
-  for (int f = 0; f < 12; ++f) { cv[f] = Cc[f * vol + i]; cl[f] = Cc[(12 + f) * vol + i]; }
-  if (MODE == PW_F) {
-    T o[3] = {T(0), T(0), T(0)};
-    bracketP(cv, cl, o);                        // P(v, L v)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) P[c * vol + i] = o[c];
-  } else {
-    T xv[12], xl[12];
-#pragma unroll
-    for (int f = 0; f < 12; ++f) { xv[f] = X[f * vol + i]; xl[f] = X[(12 + f) * vol + i]; }
-    if (MODE == PW_T) {
-      T o[3] = {T(0), T(0), T(0)};
-      bracketP(xv, cl, o);                      // P(dv, L v)
-      bracketP(cv, xl, o);                      // P(v, L dv)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) P[c * vol + i] = o[c];
-    } else {
-      T a[3] = {T(0), T(0), T(0)}, b[3] = {T(0), T(0), T(0)}, q[3] = {T(0), T(0), T(0)};
-      bracketP(cv, xl, a);                      // P(v, L U)
-      bracketP(xv, cl, b);                      // P(W, L v)
-      bracketQ(cv, xv, q);                      // Q(v, W)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        P[c * vol + i] = a[c];
-        P[(3 + c) * vol + i] = b[c];
-        P[(6 + c) * vol + i] = q[c];
-      }
-    }
-  }
-}
 
 // ---- periodic trilinear interpolation ------------------------------------------
 // Cell of the point ix - dsp on an axis of n nodes: lower node c0, upper c1,
@@ -321,15 +251,6 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const double* partial, in
 }  // namespace
 
 template <typename T>
-void pointwise(PwMode mode, const T* X, const T* C, T* P, long long vol, cudaStream_t st) {
-  switch (mode) {
-    case PW_F: k_pointwise<T, PW_F><<<blocks_for(vol), kThreads, 0, st>>>(X, C, P, vol); break;
-    case PW_T: k_pointwise<T, PW_T><<<blocks_for(vol), kThreads, 0, st>>>(X, C, P, vol); break;
-    case PW_GT: k_pointwise<T, PW_GT><<<blocks_for(vol), kThreads, 0, st>>>(X, C, P, vol); break;
-  }
-}
-
-template <typename T>
 void transport_step(const T* m, const T* vnext, const T* vcur, T* mnext, T* off, Dims g, double dt,
                     cudaStream_t st) {
   k_transport<T><<<blocks_for(g.vol()), kThreads, 0, st>>>(m, vnext, vcur, mnext, off, g, (T)dt);
@@ -377,7 +298,6 @@ void inner_V(const cplx<T>* a, const cplx<T>* b, const T* Lhat, int ncomp, long 
 }
 
 #define LDDMM_INST(T)                                                                              \
-  template void pointwise<T>(PwMode, const T*, const T*, T*, long long, cudaStream_t);           \
   template void transport_step<T>(const T*, const T*, const T*, T*, T*, Dims, double,            \
                                   cudaStream_t);                                                 \
   template void grad_dot<T>(const T*, const T*, T*, Dims, cudaStream_t);                         \

@@ -92,25 +92,36 @@ struct PiEpi {
 };
 
 // ---- transforms (dft.cu) --------------------------------------------------
-// Scratch: T1 holds [F][h1][K2][G3] complex, T2 holds [F][h1][G2][G3] complex.
+// Scratch: T2 holds [F][h1][G2][G3] complex (iota intermediate, and the C'
+// output of pi), P2 holds [9][h1][M2][M3] complex (C' of a bracket evaluation).
 template <typename T>
-void iota_batch(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat,
-                cplx<T>* T1, cplx<T>* T2, cudaStream_t st);
+void iota_batch(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2,
+                cudaStream_t st);
 template <typename T>
 void pi_batch(const Plan<T>& p, const PiSrc<T>& s, const PiEpi<T>& e, const T* Lhat,
-              cplx<T>* T1, cplx<T>* T2, cudaStream_t st);
+              cplx<T>* P2, cudaStream_t st);
 // number of kernel launches of one iota_batch / pi_batch call
-constexpr int kIotaLaunches = 3, kPiLaunches = 3;
+constexpr int kIotaLaunches = 2, kPiLaunches = 2, kBracketLaunches = 3;
+
+enum PwMode { PW_F = 0, PW_T = 1, PW_GT = 2 };
+// One bracket evaluation on the padded plan p: iota of the 24 fields of d
+// (layout per field block: value[3], jac[3][3], Lvalue[3], Ljac[3][3], with
+// jac[c][j] = d_j a_c), the bracket products, pi of the 3 (PW_F: P(v, L v),
+// PW_T: P(dv, L v) + P(v, L dv)) or 9 (PW_GT: P(v, L U), P(W, L v), Q(v, W))
+// product fields and the epilogue e.  slot holds the 24 fields of the stage
+// point: written in PW_F (d's own fields), read in PW_T and PW_GT.
+template <typename T>
+void bracket_eval(const Plan<T>& p, PwMode mode, const IotaDesc<T>& d, T* slot,
+                  const PiEpi<T>& e, const T* Lhat, cplx<T>* T2, cplx<T>* P2, cudaStream_t st);
+// largest dynamic shared memory the transform kernels need on plan p when pi
+// batches hold up to nper_max fields per component and (brackets) bracket
+// evaluations run on it; SIZE_MAX if the plan's G3 is too long for the pi
+// kernel's accumulators.  smem_limit() is the configured maximum.
+template <typename T>
+size_t max_smem_needed(const Plan<T>& p, int nper_max, bool brackets);
+size_t smem_limit();
 
 // ---- grid kernels (grid.cu) -----------------------------------------------
-enum PwMode { PW_F = 0, PW_T = 1, PW_GT = 2 };
-// Pointwise bracket products on the padded grid.  X: 24 fields of this
-// evaluation, C: 24 cached fields of the stage point, each field-block laid
-// out as value[3], jac[3][3], Lvalue[3], Ljac[3][3] (jac[c][j] = d_j a_c).
-// Output P: 3 fields (PW_F, PW_T) or 9 fields (PW_GT: A, B, Q).
-template <typename T>
-void pointwise(PwMode mode, const T* X, const T* C, T* P, long long vol, cudaStream_t st);
-
 // Semi-Lagrangian state step (Eq. 52): m_next(x) = m(X_n(x)), foot point from
 // v_next (at x) and v_cur (trilinear); also writes the displacement off[3].
 template <typename T>

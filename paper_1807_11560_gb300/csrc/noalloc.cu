@@ -4,7 +4,7 @@
 // caching allocator already holds nearly all device memory, a latency-bound
 // loop that cannot absorb the device-wide synchronisation cudaFree implies,
 // or a plugin host that forbids libraries from allocating at all.  For them
-// lddmm_iota_noalloc runs the same three transform kernels as lddmm_iota,
+// lddmm_iota_noalloc runs the same transform kernels as lddmm_iota,
 // but every intermediate lives in the fixed device array below instead of in
 // buffers of a context.  The caller passes device inputs and outputs only.
 #include <mutex>
@@ -92,9 +92,8 @@ extern "C" int lddmm_iota_noalloc(int ndim, const int* grid, const int* K, const
   const size_t c8 = sizeof(float2);
   const size_t s3 = align256((size_t)b.k3 * N.n3 * c8), s2 = align256((size_t)b.k2 * N.n2 * c8),
                s1 = align256((size_t)b.h1 * N.n1 * c8), sh = align256((size_t)ncomp * b.vol() * c8),
-               st1 = align256((size_t)ncomp * b.h1 * b.k2 * N.n3 * c8),
                st2 = align256((size_t)ncomp * b.h1 * N.n2 * N.n3 * c8);
-  if (s3 + s2 + s1 + sh + st1 + st2 > kNoAllocBytes) return LDDMM_ENOMEM;
+  if (s3 + s2 + s1 + sh + st2 > kNoAllocBytes) return LDDMM_ENOMEM;
 
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -116,8 +115,8 @@ extern "C" int lddmm_iota_noalloc(int ndim, const int* grid, const int* K, const
   p.E2f = reinterpret_cast<float2*>(base + s3);
   p.E1f = reinterpret_cast<float2*>(base + s3 + s2);
   float2* herm = reinterpret_cast<float2*>(base + s3 + s2 + s1);
-  float2* T1 = reinterpret_cast<float2*>(base + s3 + s2 + s1 + sh);
-  float2* T2 = reinterpret_cast<float2*>(base + s3 + s2 + s1 + sh + st1);
+  float2* T2 = reinterpret_cast<float2*>(base + s3 + s2 + s1 + sh);
+  if (max_smem_needed<float>(p, 1, false) > smem_limit()) return LDDMM_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
   const long long ntw = (long long)b.k3 * N.n3 + (long long)b.k2 * N.n2 + (long long)b.h1 * N.n1;
@@ -132,6 +131,6 @@ extern "C" int lddmm_iota_noalloc(int ndim, const int* grid, const int* K, const
     d.applyL[c] = 0;
   }
   // applyL is off for every field, so the symbol table is never read
-  iota_batch<float>(p, d, reinterpret_cast<const float*>(herm), T1, T2, st);
+  iota_batch<float>(p, d, reinterpret_cast<const float*>(herm), T2, st);
   return cudaGetLastError() == cudaSuccess ? LDDMM_OK : LDDMM_ECUDA;
 }
