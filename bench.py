@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="3d_64_ellipsoids")
-    ap.add_argument("--probe", default="inc_step", help="kernel class timed for the roofline")
+    ap.add_argument("--probe", default="auto", help="kernel class timed for the roofline (auto: dominant)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -167,15 +167,22 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- GPU arm
-def algorithmic_work(cls, Ns, Ks, Nt):
-    """(bound, per-launch algorithmic amount, unit) of a probed kernel class."""
-    import numpy as np
-    nvox = int(np.prod(Ns))
-    if cls == "inc_step":
-        return "hbm", 12.0 * nvox, "B"          # read m_n, dm_n; write dm_{n+1}
-    if cls == "transport":
-        return "hbm", 8.0 * nvox, "B"           # read m_n; write m_{n+1}
-    raise ValueError(cls)
+PROBE_CLASSES = ("iota_ab", "cpw", "pi_ba", "inc_step", "transport", "iota_full", "pi_full")
+HBM_CLASSES = ("inc_step", "transport")
+SMS, FP32_LANES = 152, 128
+
+
+def pick_dominant(ctx, v, n_pcg):
+    """Probe every kernel class over one GN iteration (untimed); return the class
+    with the largest total device time and the per-class totals (ms)."""
+    totals = {}
+    for cls in PROBE_CLASSES:
+        ctx.probe(cls)
+        w = v.clone()
+        ctx.gn_solve(w, 1, n_pcg)
+        totals[cls] = ctx.probe_read()[0]
+    ctx.probe(None)
+    return max(totals, key=totals.get), totals
 
 
 def run_gpu(args):
@@ -202,11 +209,13 @@ def run_gpu(args):
     ctx.set_images(I0d, I1d)
     v = torch.zeros((d,) + tuple(Ks), dtype=torch.complex64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    ctx.probe(args.probe)
+    class_ms = None
+    probe_cls = args.probe
+    if probe_cls == "auto":
+        probe_cls, class_ms = pick_dominant(ctx, v, N_PCG)
 
     for _ in range(args.warmup):
         ctx.gn_solve(v, 1, N_PCG)
-    ctx.probe_read()                                      # discard warm-up probe time
 
     def barrier():
         if world > 1:
@@ -237,7 +246,20 @@ def run_gpu(args):
     launches = ctx.kernel_count - k0
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_dev = sum(step_ms) / 1e3
-    probe_ms, probe_n = ctx.probe_read()
+    # roofline pass: the same K steps again with CUDA events around every
+    # launch of the dominant kernel class (events perturb the step time, so
+    # the headline value above is taken without them)
+    ctx.probe(probe_cls)
+    w = v.clone()
+    ctx.gn_solve(w, 1, N_PCG)                             # builds the probed graph
+    ctx.probe_read()
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ctx.gn_solve(w, 1, N_PCG)
+    barrier()
+    probe_ms, probe_n, probe_work = ctx.probe_read()
+    ctx.probe(None)
 
     tt = torch.tensor([t_dev, float(hv)], dtype=torch.float64, device=dev)
     if world > 1:
@@ -289,16 +311,28 @@ def run_gpu(args):
 
     if rank == 0:
         peaks, src = load_peaks()
-        bound, work, wunit = algorithmic_work(args.probe, Ns, Ks, Nt)
         avg_s = (probe_ms / 1e3) / max(probe_n, 1)
-        if bound == "hbm":
+        work = probe_work / max(probe_n, 1)
+        if probe_cls in HBM_CLASSES:
             achieved = work / avg_s / 1e9
             peak = peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
-            runit = "GB/s"
-        roof = {"bound": bound, "kernel": args.probe, "achieved": achieved, "peak": peak, "unit": runit,
-                "frac": achieved / peak, "traffic": None, "peak_source": f"{src} (of {src})",
-                "launches_timed": probe_n, "avg_launch_us": avg_s * 1e6,
-                "algorithmic_per_launch": work, "algorithmic_unit": wunit}
+            roof = {"bound": "hbm", "unit": "GB/s", "peak_source": f"{src} HBM copy bandwidth (of {src})"}
+            wunit = "B"
+        else:
+            mhz = clk.get("sm_mhz") or 2070.0
+            achieved = work / avg_s / 1e12
+            peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+            roof = {"bound": "alu", "unit": "TFLOP/s",
+                    "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz "
+                                   "(median sampled SM clock); FP32 SIMT contraction"}
+            wunit = "flop"
+        roof.update({"kernel": probe_cls, "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                     "traffic": None, "launches_timed": probe_n, "avg_launch_us": avg_s * 1e6,
+                     "algorithmic_per_launch": work, "algorithmic_unit": wunit,
+                     "measured": f"CUDA events around each launch over a second pass of the {args.steps} "
+                                 "timed steps"})
+        if class_ms:
+            roof["class_ms_one_gn_iteration"] = class_ms
         cpu = None
         if not args.no_cpu_baseline:
             times = oracle_hessvec_rate(name, 3)

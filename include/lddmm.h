@@ -106,7 +106,7 @@ void lddmm_default_opts(lddmm_opts* opts);
 
 /* Create a registration context (Section 3.2).
  *   ndim    2 or 3.
- *   grid    ndim image sizes N_j >= 2 (int array, host).
+ *   grid    ndim image sizes N_j >= 2, N_1 N_2 N_3 < 2^31 (int array, host).
  *   K       ndim band sizes: even, 2 <= K_j <= min(N_j, 512) (int array, host).
  *   alpha   > 0, s >= 1: L = (Id - alpha Lap)^s (Eq. 1).
  *   sigma   > 0: data weight 1/sigma^2 (Eq. 50).
@@ -212,18 +212,25 @@ int lddmm_last_dm1(lddmm_ctx* ctx, void* dm1_out);
 
 /* Timing probe.  Brackets every launch of one kernel class with CUDA events
  * on the stream it runs on (also inside the captured Hessian-vector graph)
- * and accumulates the elapsed device time.  kernel_class is one of
- * "transport" (state step, Eq. 52), "inc_step" (incremental state step,
- * Eq. 31), "bracket" (one bracket evaluation of ad~* / ad~ on the padded
- * product grid: its three kernels), "iota_full" / "pi_full" (transforms on
- * the image grid); NULL or "" switches the probe off.  Changing the class
- * rebuilds the graph on the next product.  Not part of the method; the
- * paper has no counterpart. */
+ * and accumulates the elapsed device time and the algorithmic work of each
+ * timed launch.  kernel_class is one of
+ *   "transport"  semi-Lagrangian state step (Eq. 52); work = 8 N bytes
+ *                (read m_n, write m_{n+1});
+ *   "inc_step"   incremental state step (Eq. 31); work = 12 N bytes
+ *                (read m_n and dm_n, write dm_{n+1});
+ *   "iota_ab", "cpw", "pi_ba"  the three kernels of a bracket evaluation on
+ *                the padded product grid (Eqs. 48-49); work = flops of their
+ *                contractions and bracket products;
+ *   "iota_full", "pi_full"  transforms on the image grid; work = flops;
+ * NULL or "" switches the probe off.  Changing the class rebuilds the graph
+ * on the next product.  Not part of the method; the paper has no
+ * counterpart. */
 int lddmm_probe(lddmm_ctx* ctx, const char* kernel_class);
 
-/* Accumulated probe time (ms) and number of timed launches since the last
- * read or lddmm_probe call; resets both. */
-int lddmm_probe_read(lddmm_ctx* ctx, double* total_ms, long long* launches);
+/* Accumulated probe time (ms), number of timed launches and algorithmic work
+ * (bytes or flops, see lddmm_probe) since the last read or lddmm_probe call;
+ * resets all three. */
+int lddmm_probe_read(lddmm_ctx* ctx, double* total_ms, long long* launches, double* work);
 
 /* Number of CUDA kernels this context has launched since creation (graph
  * replays count each kernel node). */

@@ -41,9 +41,10 @@ struct Fail {
   int code;
 };
 
-enum ProbeClass { PR_TRANSPORT = 0, PR_INC, PR_BRACKET, PR_IOTA_FULL, PR_PI_FULL, PR_COUNT };
-const char* const kProbeNames[PR_COUNT] = {"transport", "inc_step", "bracket", "iota_full",
-                                           "pi_full"};
+enum ProbeClass { PR_TRANSPORT = 0, PR_INC, PR_IOTA_AB, PR_CPW, PR_PI_BA, PR_IOTA_FULL, PR_PI_FULL,
+                  PR_COUNT };
+const char* const kProbeNames[PR_COUNT] = {"transport", "inc_step", "iota_ab", "cpw", "pi_ba",
+                                           "iota_full", "pi_full"};
 
 template <typename T>
 struct State {
@@ -100,8 +101,9 @@ struct Impl {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend_direct, graph_pairs;
   std::vector<cudaEvent_t> graph_events;
   bool graph_pending = false;
-  double probe_ms = 0.0;
+  double probe_ms = 0.0, probe_work = 0.0;
   long long probe_n = 0;
+  std::vector<double> pend_work, graph_work;
 
   // ---------------------------------------------------------------- utils
   void cuda(cudaError_t e, const char* what) {
@@ -299,25 +301,30 @@ struct Impl {
     pstart = probe_event();
     probe_record(pstart);
   }
-  void pe(int cls) {
+  // work: algorithmic flops (transforms, brackets) or bytes (transport steps)
+  void pe(int cls, double work) {
     if (cls != probe) return;
     cudaEvent_t e = probe_event();
     probe_record(e);
     (capturing ? graph_pairs : pend_direct).push_back({pstart, e});
+    (capturing ? graph_work : pend_work).push_back(work);
   }
   void collect() {
     float ms = 0.f;
-    for (auto& pr : pend_direct) {
-      cuda(cudaEventElapsedTime(&ms, pr.first, pr.second), "probe elapsed");
+    for (size_t i = 0; i < pend_direct.size(); ++i) {
+      cuda(cudaEventElapsedTime(&ms, pend_direct[i].first, pend_direct[i].second), "probe elapsed");
       probe_ms += ms;
+      probe_work += pend_work[i];
       ++probe_n;
     }
     pend_direct.clear();
+    pend_work.clear();
     evnext = 0;
     if (graph_pending) {
-      for (auto& pr : graph_pairs) {
-        cuda(cudaEventElapsedTime(&ms, pr.first, pr.second), "probe elapsed");
+      for (size_t i = 0; i < graph_pairs.size(); ++i) {
+        cuda(cudaEventElapsedTime(&ms, graph_pairs[i].first, graph_pairs[i].second), "probe elapsed");
         probe_ms += ms;
+        probe_work += graph_work[i];
         ++probe_n;
       }
       graph_pending = false;
@@ -370,11 +377,27 @@ struct Impl {
 
   // one evaluation of a bracket expression at a Heun stage point
   void eval(PwMode mode, T* slot, const C* srcA, const C* srcB, const PiEpi<T>& e) {
-    pb(PR_BRACKET);
-    bracket_eval<T>(pad, mode, block24(srcA, srcB, slot), slot, e, Lhat, T2, P2, st);
-    pe(PR_BRACKET);
+    const double H1 = K.h1, K2 = K.k2, K3 = K.k3, M1 = M.n1, M2 = M.n2, M3 = M.n3;
+    const int NP = (mode == PW_GT) ? 9 : 3;
+    const double bflops = mode == PW_F ? 44.0 : (mode == PW_T ? 88.0 : 124.0);
+    pb(PR_IOTA_AB);
+    bracket_iota<T>(pad, block24(srcA, srcB, slot), Lhat, T2, st);
+    pe(PR_IOTA_AB, 8.0 * 24 * H1 * (K2 * K3 * M3 + K2 * M2 * M3));
+    pb(PR_CPW);
+    bracket_cpw<T>(pad, mode, T2, slot, P2, st);
+    pe(PR_CPW, 4.0 * (24 + NP) * H1 * (double)Mvol + bflops * (double)Mvol);
+    pb(PR_PI_BA);
+    bracket_pi<T>(pad, e, Lhat, P2, st);
+    pe(PR_PI_BA, 8.0 * 3 * e.nper * H1 * (K2 * M2 * M3 + K2 * K3 * M3));
     launches += kBracketLaunches;
     check_launch("bracket evaluation");
+  }
+
+  // algorithmic flops of iota (or pi) of nf scalar fields on the image grid,
+  // Hermitian half spectrum along axis 1
+  double iota_flops(int nf) const {
+    const double H1 = K.h1, K2 = K.k2, K3 = K.k3;
+    return nf * (8.0 * H1 * (K2 * K3 * N.n3 + K2 * (double)N.n2 * N.n3) + 4.0 * H1 * (double)Nvol);
   }
 
   // iota of `count` BL vectors (3 comps each) onto the image grid
@@ -393,7 +416,7 @@ struct Impl {
         }
       pb(PR_IOTA_FULL);
       iota_batch<T>(full, d, Lhat, T2, st);
-      pe(PR_IOTA_FULL);
+      pe(PR_IOTA_FULL, iota_flops(d.nf));
       launches += kIotaLaunches;
     }
     check_launch("iota to image grid");
@@ -411,7 +434,7 @@ struct Impl {
     add_out(e, out, 0, 1.0, {});
     pb(PR_PI_FULL);
     pi_batch<T>(full, ps, e, Lhat, T2, st);
-    pe(PR_PI_FULL);
+    pe(PR_PI_FULL, iota_flops(3));
     launches += kPiLaunches;
     check_launch("projection");
   }
@@ -452,7 +475,7 @@ struct Impl {
       transport_step<T>(S.mh + n * Nvol, S.vgrid + (long long)(n + 1) * 3 * Nvol,
                         S.vgrid + (long long)n * 3 * Nvol, S.mh + (n + 1) * Nvol,
                         S.off + (long long)n * 3 * Nvol, N, dt, st);
-      pe(PR_TRANSPORT);
+      pe(PR_TRANSPORT, 8.0 * (double)Nvol);
     }
     launches += Nt;
     check_launch("transport");
@@ -542,7 +565,7 @@ struct Impl {
       inc_step<T>(n == 0 ? nullptr : dm[n & 1], sb[n & 1], S.mh + (long long)(n + 1) * Nvol,
                   dvgrid + (long long)(n + 1) * 3 * Nvol, S.off + (long long)n * 3 * Nvol,
                   dm[(n + 1) & 1], sb[(n + 1) & 1], N, dt, st);
-      pe(PR_INC);
+      pe(PR_INC, 12.0 * (double)Nvol);
     }
     launches += Nt;
     terminal_field<T>(S.mh + (long long)Nt * Nvol, dm[Nt & 1], 0, -2.0 / (sigma * sigma), fterm, N, st);
@@ -625,6 +648,7 @@ struct Impl {
     for (cudaEvent_t e : graph_events) cudaEventDestroy(e);
     graph_events.clear();
     graph_pairs.clear();
+    graph_work.clear();
     graph_pending = false;
   }
 
@@ -633,6 +657,7 @@ struct Impl {
     if (cls != probe) invalidate_graph();
     probe = cls;
     probe_ms = 0.0;
+    probe_work = 0.0;
     probe_n = 0;
   }
 
@@ -934,6 +959,9 @@ int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, doubl
     if (grid[j] < 2 || K[j] < 2 || (K[j] & 1) || K[j] > grid[j] || grid[j] > (1 << 16) || K[j] > 512)
       return LDDMM_EINVAL;
   }
+  long long nvox = 1;
+  for (int j = 0; j < ndim; ++j) nvox *= grid[j];
+  if (nvox >= (1LL << 31)) return LDDMM_EINVAL;
   lddmm_opts o;
   lddmm_default_opts(&o);
   if (opts) o = *opts;
@@ -1057,14 +1085,17 @@ int lddmm_probe(lddmm_ctx* ctx, const char* kernel_class) {
   return lddmm::dispatch(ctx, [&](auto& im) { im.set_probe(cls); });
 }
 
-int lddmm_probe_read(lddmm_ctx* ctx, double* total_ms, long long* launches) {
+int lddmm_probe_read(lddmm_ctx* ctx, double* total_ms, long long* launches, double* work) {
   if (!ctx) return LDDMM_EINVAL;
-  if (bad_ptr(ctx, total_ms, "total_ms") || bad_ptr(ctx, launches, "launches")) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, total_ms, "total_ms") || bad_ptr(ctx, launches, "launches") || bad_ptr(ctx, work, "work"))
+    return LDDMM_EINVAL;
   return lddmm::dispatch(ctx, [&](auto& im) {
     im.sync("probe read");
     *total_ms = im.probe_ms;
     *launches = im.probe_n;
+    *work = im.probe_work;
     im.probe_ms = 0.0;
+    im.probe_work = 0.0;
     im.probe_n = 0;
   });
 }

@@ -521,9 +521,12 @@ void pi_batch(const Plan<T>& p, const PiSrc<T>& s, const PiEpi<T>& e, const T* L
 }
 
 template <typename T>
-void bracket_eval(const Plan<T>& p, PwMode mode, const IotaDesc<T>& d, T* slot, const PiEpi<T>& e,
-                  const T* Lhat, cplx<T>* T2, cplx<T>* P2, cudaStream_t st) {
+void bracket_iota(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2, cudaStream_t st) {
   launch_iota_AB<T>(p, d, Lhat, T2, st);
+}
+
+template <typename T>
+void bracket_cpw(const Plan<T>& p, PwMode mode, const cplx<T>* T2, T* slot, cplx<T>* P2, cudaStream_t st) {
   const int TP = cpw_tile(p);
   const int NP = (mode == PW_GT) ? 9 : 3;
   const size_t smem = cpw_smem(p, TP, NP);
@@ -543,6 +546,10 @@ void bracket_eval(const Plan<T>& p, PwMode mode, const IotaDesc<T>& d, T* slot, 
       k_cpw<T, PW_GT><<<grid, kThreads, smem, st>>>(p, T2, slot, P2, TP);
       break;
   }
+}
+
+template <typename T>
+void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T>* P2, cudaStream_t st) {
   launch_pi_BA<T>(p, e, Lhat, P2, st);
 }
 
@@ -551,8 +558,9 @@ void bracket_eval(const Plan<T>& p, PwMode mode, const IotaDesc<T>& d, T* slot, 
   template void iota_batch<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t); \
   template void pi_batch<T>(const Plan<T>&, const PiSrc<T>&, const PiEpi<T>&, const T*, cplx<T>*,  \
                             cudaStream_t);                                                         \
-  template void bracket_eval<T>(const Plan<T>&, PwMode, const IotaDesc<T>&, T*, const PiEpi<T>&,  \
-                                const T*, cplx<T>*, cplx<T>*, cudaStream_t);
+  template void bracket_iota<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t); \
+  template void bracket_cpw<T>(const Plan<T>&, PwMode, const cplx<T>*, T*, cplx<T>*, cudaStream_t); \
+  template void bracket_pi<T>(const Plan<T>&, const PiEpi<T>&, const T*, const cplx<T>*, cudaStream_t);
 LDDMM_DFT_INST(float)
 LDDMM_DFT_INST(double)
 

@@ -26,15 +26,17 @@ __device__ __forceinline__ void cell(int ix, T dsp, int n, int& c0, int& c1, T& 
   w = nd - fl;
   // a non-finite or absurd displacement keeps its NaN weight but a safe index
   if (!(fabs(fl) < T(1e6))) fl = T(0);
-  int c = (ix + (int)fl) % n;
-  if (c < 0) c += n;
+  int c = ix + (int)fl;
+  if ((unsigned)c >= (unsigned)n) {          // rare: more than one period away
+    c %= n;
+    if (c < 0) c += n;
+  }
   c0 = c;
   c1 = (c + 1 == n) ? 0 : c + 1;
 }
 
-template <typename T>
-__device__ __forceinline__ void corners(const int* c0, const int* c1, int n2, int n3, long long* o) {
-  const long long a0 = (long long)c0[0] * n2, a1 = (long long)c1[0] * n2;
+__device__ __forceinline__ void corners(const int* c0, const int* c1, int n2, int n3, int* o) {
+  const int a0 = c0[0] * n2, a1 = c1[0] * n2;
   o[0] = (a0 + c0[1]) * n3 + c0[2];
   o[1] = (a0 + c0[1]) * n3 + c1[2];
   o[2] = (a0 + c1[1]) * n3 + c0[2];
@@ -46,7 +48,7 @@ __device__ __forceinline__ void corners(const int* c0, const int* c1, int n2, in
 }
 
 template <typename T>
-__device__ __forceinline__ T trilin(const T* __restrict__ f, const long long* o, const T* w) {
+__device__ __forceinline__ T trilin(const T* __restrict__ f, const int* o, const T* w) {
   const T u0 = f[o[0]] + w[2] * (f[o[1]] - f[o[0]]);
   const T u1 = f[o[2]] + w[2] * (f[o[3]] - f[o[2]]);
   const T u2 = f[o[4]] + w[2] * (f[o[5]] - f[o[4]]);
@@ -56,11 +58,13 @@ __device__ __forceinline__ T trilin(const T* __restrict__ f, const long long* o,
   return v0 + w[0] * (v1 - v0);
 }
 
-__device__ __forceinline__ void unflat(long long idx, int n2, int n3, int* ix) {
-  ix[2] = (int)(idx % n3);
-  const long long r = idx / n3;
-  ix[1] = (int)(r % n2);
-  ix[0] = (int)(r / n2);
+// grid index of a flat voxel index (volumes stay below 2^31)
+__device__ __forceinline__ void unflat(unsigned idx, unsigned n2, unsigned n3, int* ix) {
+  const unsigned r = idx / n3;
+  ix[2] = (int)(idx - r * n3);
+  const unsigned q = r / n2;
+  ix[1] = (int)(r - q * n2);
+  ix[0] = (int)q;
 }
 
 // central difference d_j m at grid index ix (periodic), in unit-domain units
@@ -70,8 +74,8 @@ __device__ __forceinline__ T cdiff(const T* __restrict__ m, const int* ix, int j
   int p[3] = {ix[0], ix[1], ix[2]}, q[3] = {ix[0], ix[1], ix[2]};
   p[j] = (ix[j] + 1 == n[j]) ? 0 : ix[j] + 1;
   q[j] = (ix[j] == 0) ? n[j] - 1 : ix[j] - 1;
-  const T mp = m[((long long)p[0] * g.n2 + p[1]) * g.n3 + p[2]];
-  const T mq = m[((long long)q[0] * g.n2 + q[1]) * g.n3 + q[2]];
+  const T mp = m[(p[0] * g.n2 + p[1]) * g.n3 + p[2]];
+  const T mq = m[(q[0] * g.n2 + q[1]) * g.n3 + q[2]];
   return (mp - mq) * (T(0.5) * T(n[j]));
 }
 
@@ -80,20 +84,20 @@ __global__ void __launch_bounds__(kThreads)
 k_transport(const T* __restrict__ m, const T* __restrict__ vn, const T* __restrict__ vc,
             T* __restrict__ mn, T* __restrict__ off, Dims g, T dt) {
   const long long vol = g.vol();
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= vol) return;
   int ix[3];
   unflat(idx, g.n2, g.n3, ix);
   const int n[3] = {g.n1, g.n2, g.n3};
   T a[3], c0w[3];
   int c0[3], c1[3];
-  long long o[8];
+  int o[8];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     a[j] = vn[j * vol + idx];
     cell(ix[j], dt * T(n[j]) * a[j], n[j], c0[j], c1[j], c0w[j]);
   }
-  corners<T>(c0, c1, g.n2, g.n3, o);
+  corners(c0, c1, g.n2, g.n3, o);
   T dsp[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
@@ -102,7 +106,7 @@ k_transport(const T* __restrict__ m, const T* __restrict__ vn, const T* __restri
   }
 #pragma unroll
   for (int j = 0; j < 3; ++j) cell(ix[j], dsp[j], n[j], c0[j], c1[j], c0w[j]);
-  corners<T>(c0, c1, g.n2, g.n3, o);
+  corners(c0, c1, g.n2, g.n3, o);
   mn[idx] = trilin(m, o, c0w);
 #pragma unroll
   for (int j = 0; j < 3; ++j) off[j * vol + idx] = dsp[j];
@@ -112,7 +116,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_grad_dot(const T* __restrict__ m, const T* __restrict__ dv, T* __restrict__ s, Dims g) {
   const long long vol = g.vol();
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= vol) return;
   int ix[3];
   unflat(idx, g.n2, g.n3, ix);
@@ -128,7 +132,7 @@ k_inc_step(const T* __restrict__ dm, const T* __restrict__ s, const T* __restric
            const T* __restrict__ dvn, const T* __restrict__ off, T* __restrict__ dmn,
            T* __restrict__ sn, Dims g, T dt) {
   const long long vol = g.vol();
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= vol) return;
   int ix[3];
   unflat(idx, g.n2, g.n3, ix);
@@ -138,10 +142,10 @@ k_inc_step(const T* __restrict__ dm, const T* __restrict__ s, const T* __restric
   for (int j = 0; j < 3; ++j) snew = fma(cdiff(mnext, ix, j, g), dvn[j * vol + idx], snew);
   int c0[3], c1[3];
   T w[3];
-  long long o[8];
+  int o[8];
 #pragma unroll
   for (int j = 0; j < 3; ++j) cell(ix[j], off[j * vol + idx], n[j], c0[j], c1[j], w[j]);
-  corners<T>(c0, c1, g.n2, g.n3, o);
+  corners(c0, c1, g.n2, g.n3, o);
   const T dmi = dm ? trilin(dm, o, w) : T(0);
   const T si = trilin(s, o, w);
   dmn[idx] = dmi - T(0.5) * dt * (si + snew);
@@ -153,7 +157,7 @@ __global__ void __launch_bounds__(kThreads)
 k_terminal(const T* __restrict__ m, const T* __restrict__ y, int diff, T coef, T* __restrict__ out,
            Dims g) {
   const long long vol = g.vol();
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= vol) return;
   int ix[3];
   unflat(idx, g.n2, g.n3, ix);

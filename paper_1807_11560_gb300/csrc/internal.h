@@ -104,15 +104,25 @@ void pi_batch(const Plan<T>& p, const PiSrc<T>& s, const PiEpi<T>& e, const T* L
 constexpr int kIotaLaunches = 2, kPiLaunches = 2, kBracketLaunches = 3;
 
 enum PwMode { PW_F = 0, PW_T = 1, PW_GT = 2 };
-// One bracket evaluation on the padded plan p: iota of the 24 fields of d
-// (layout per field block: value[3], jac[3][3], Lvalue[3], Ljac[3][3], with
-// jac[c][j] = d_j a_c), the bracket products, pi of the 3 (PW_F: P(v, L v),
-// PW_T: P(dv, L v) + P(v, L dv)) or 9 (PW_GT: P(v, L U), P(W, L v), Q(v, W))
-// product fields and the epilogue e.  slot holds the 24 fields of the stage
-// point: written in PW_F (d's own fields), read in PW_T and PW_GT.
+// One bracket evaluation on the padded plan p runs three kernels:
+//   bracket_iota  iota stages A+B of the 24 fields of d (layout per field
+//                 block: value[3], jac[3][3], Lvalue[3], Ljac[3][3], with
+//                 jac[c][j] = d_j a_c) -> T2;
+//   bracket_cpw   stage C, the bracket products and pi stage C' of the 3
+//                 (PW_F: P(v, L v); PW_T: P(dv, L v) + P(v, L dv)) or 9
+//                 (PW_GT: P(v, L U), P(W, L v), Q(v, W)) product fields -> P2;
+//                 slot holds the 24 fields of the stage point, written in PW_F
+//                 (d's own fields) and read in PW_T and PW_GT;
+//   bracket_pi    pi stages B'+A' of P2 and the epilogue e.
 template <typename T>
-void bracket_eval(const Plan<T>& p, PwMode mode, const IotaDesc<T>& d, T* slot,
-                  const PiEpi<T>& e, const T* Lhat, cplx<T>* T2, cplx<T>* P2, cudaStream_t st);
+void bracket_iota(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2,
+                  cudaStream_t st);
+template <typename T>
+void bracket_cpw(const Plan<T>& p, PwMode mode, const cplx<T>* T2, T* slot, cplx<T>* P2,
+                 cudaStream_t st);
+template <typename T>
+void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T>* P2,
+                cudaStream_t st);
 // largest dynamic shared memory the transform kernels need on plan p when pi
 // batches hold up to nper_max fields per component and (brackets) bracket
 // evaluations run on it; SIZE_MAX if the plan's G3 is too long for the pi

@@ -70,7 +70,8 @@ def lib():
         "lddmm_last_dm1": (I, [P, P]),
         "lddmm_kernel_count": (ctypes.c_longlong, [P]),
         "lddmm_probe": (I, [P, ctypes.c_char_p]),
-        "lddmm_probe_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]),
+        "lddmm_probe_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(D)]),
         "lddmm_iota_noalloc": (I, [I, ctypes.POINTER(I), ctypes.POINTER(I), P, I, P, P]),
         "lddmm_last_error": (ctypes.c_char_p, [P]),
         "lddmm_destroy": (None, [P]),
@@ -250,10 +251,10 @@ class Context:
         self._check(lib().lddmm_probe(self._h, (kernel_class or "").encode()))
 
     def probe_read(self):
-        """(total device ms, timed launches) since the last read."""
-        ms, n = ctypes.c_double(), ctypes.c_longlong()
-        self._check(lib().lddmm_probe_read(self._h, ctypes.byref(ms), ctypes.byref(n)))
-        return ms.value, n.value
+        """(total device ms, timed launches, algorithmic work) since the last read."""
+        ms, n, w = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+        self._check(lib().lddmm_probe_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
+        return ms.value, n.value, w.value
 
     @property
     def kernel_count(self):
