@@ -167,7 +167,7 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- GPU arm
-PROBE_CLASSES = ("iota_ab", "cpw", "pi_ba", "inc_step", "transport", "iota_full", "pi_full")
+PROBE_CLASSES = ("sweep", "iota_ab", "cpw", "pi_ba", "inc_step", "transport", "iota_full", "pi_full")
 HBM_CLASSES = ("inc_step", "transport")
 SMS, FP32_LANES = 152, 128
 

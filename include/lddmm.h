@@ -69,7 +69,7 @@ typedef enum {
   LDDMM_ECUDA = 3,       /* a CUDA call failed; see lddmm_last_error */
   LDDMM_ESTATE = 4,      /* call out of order (e.g. hessvec before gradient) */
   LDDMM_ENONFINITE = 5,  /* energy or gradient became NaN/Inf */
-  LDDMM_ETIMEOUT = 6,    /* reserved: a bounded device wait gave up */
+  LDDMM_ETIMEOUT = 6,    /* a bounded device wait (persistent-sweep barrier) gave up */
   LDDMM_ENOTCONV = 7     /* reserved for callers; gn_solve reports line-search
                             failure in lddmm_report.ls_failed instead */
 } lddmm_status;
@@ -83,6 +83,9 @@ typedef struct {
   double armijo_c;      /* Armijo constant; default 1e-4 */
   int max_halvings;     /* line-search halvings of eps = 1; default 10 */
   int use_graphs;       /* replay the Hessian-vector product from a CUDA graph; default 1 */
+  int persistent;       /* run each band-limited time sweep as one persistent cooperative
+                           kernel (grid barriers with bounded waits); 0 launches three
+                           kernels per bracket evaluation instead; default 1 */
 } lddmm_opts;
 
 /* Report of lddmm_gn_solve.  The per-iteration arrays are optional
@@ -101,7 +104,7 @@ typedef struct {
 } lddmm_report;
 
 /* Defaults for lddmm_opts (precision FP32, legacy stream, tol 1e-12,
- * c = 1e-4, 10 halvings, graphs on). */
+ * c = 1e-4, 10 halvings, graphs on, persistent sweeps on). */
 void lddmm_default_opts(lddmm_opts* opts);
 
 /* Create a registration context (Section 3.2).
@@ -222,6 +225,7 @@ int lddmm_last_dm1(lddmm_ctx* ctx, void* dm1_out);
  *                the padded product grid (Eqs. 48-49); work = flops of their
  *                contractions and bracket products;
  *   "iota_full", "pi_full"  transforms on the image grid; work = flops;
+ *   "sweep"      one persistent band-limited sweep kernel; work = flops;
  * NULL or "" switches the probe off.  Changing the class rebuilds the graph
  * on the next product.  Not part of the method; the paper has no
  * counterpart. */

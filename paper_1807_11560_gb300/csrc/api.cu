@@ -42,9 +42,9 @@ struct Fail {
 };
 
 enum ProbeClass { PR_TRANSPORT = 0, PR_INC, PR_IOTA_AB, PR_CPW, PR_PI_BA, PR_IOTA_FULL, PR_PI_FULL,
-                  PR_COUNT };
+                  PR_SWEEP, PR_COUNT };
 const char* const kProbeNames[PR_COUNT] = {"transport", "inc_step", "iota_ab", "cpw", "pi_ba",
-                                           "iota_full", "pi_full"};
+                                           "iota_full", "pi_full", "sweep"};
 
 template <typename T>
 struct State {
@@ -81,8 +81,14 @@ struct Impl {
   T* dvgrid = nullptr;       // [Nt+1][3][Nvol]
   T *dm[2] = {nullptr, nullptr}, *sb[2] = {nullptr, nullptr};
   T* fterm = nullptr;        // [3][Nvol]
-  double *partial = nullptr, *dres = nullptr;
+  double *partial = nullptr, *dres = nullptr;   // dres[7]: sweep barrier time-out flag
   double* hres = nullptr;    // pinned host mirror of dres
+  // persistent sweeps: evaluation descriptors recorded once at creation
+  std::vector<EvalDesc<T>>* rec = nullptr;
+  EvalDesc<T> *ev_shoot_lin = nullptr, *ev_shoot_trial = nullptr, *ev_tangent = nullptr,
+              *ev_backward = nullptr;
+  unsigned* bar = nullptr;
+  double sweep_flops[3] = {0, 0, 0};   // algorithmic flops of one sweep per mode
   long long launches = 0;
   std::vector<void*> allocs;
   // graph of one Hessian-vector product (input dvh[0], output vout)
@@ -253,8 +259,43 @@ struct Impl {
     alloc(fterm, (size_t)3 * Nvol);
     alloc(partial, (size_t)kReduceBlocks);
     alloc(dres, 8);
+    cuda(cudaMemset(dres, 0, 8 * sizeof(double)), "memset");
     cuda(cudaMallocHost(&hres, 8 * sizeof(double)), "cudaMallocHost");
+    alloc(bar, 2);
+    record_sweeps();
     cuda(cudaDeviceSynchronize(), "create");
+  }
+
+  // descriptors of every persistent sweep, recorded by running the sweep
+  // loops once without launching anything
+  void record_sweeps() {
+    std::vector<EvalDesc<T>> v;
+    rec = &v;
+    auto upload = [&](EvalDesc<T>*& dst) {
+      alloc(dst, v.size());
+      cuda(cudaMemcpy(dst, v.data(), v.size() * sizeof(EvalDesc<T>), cudaMemcpyHostToDevice), "descriptors");
+      v.clear();
+    };
+    shoot(lin);
+    upload(ev_shoot_lin);
+    shoot(trial);
+    upload(ev_shoot_trial);
+    tangent(lin);
+    upload(ev_tangent);
+    backward(lin);
+    upload(ev_backward);
+    rec = nullptr;
+    sweep_flops[PW_F] = 2.0 * Nt * (flops_iota_ab() + flops_cpw(PW_F) + flops_pi_ba(1));
+    sweep_flops[PW_T] = 2.0 * Nt * (flops_iota_ab() + flops_cpw(PW_T) + flops_pi_ba(1));
+    sweep_flops[PW_GT] = 2.0 * Nt * (flops_iota_ab() + flops_cpw(PW_GT) + flops_pi_ba(3));
+  }
+
+  // a persistent sweep whose barrier wait gave up left dres[7] = 1
+  void check_flag(double f) {
+    if (f != 0.0) {
+      *err = "a persistent sweep barrier wait timed out";
+      throw Fail{LDDMM_ETIMEOUT};
+    }
   }
 
   // ------------------------------------------------------------ staging
@@ -376,22 +417,47 @@ struct Impl {
   }
 
   // one evaluation of a bracket expression at a Heun stage point
-  void eval(PwMode mode, T* slot, const C* srcA, const C* srcB, const PiEpi<T>& e) {
-    const double H1 = K.h1, K2 = K.k2, K3 = K.k3, M1 = M.n1, M2 = M.n2, M3 = M.n3;
+  // algorithmic flops of the three phases of one bracket evaluation
+  double flops_iota_ab() const {
+    const double H1 = K.h1, K2 = K.k2, K3 = K.k3, M2 = M.n2, M3 = M.n3;
+    return 8.0 * 24 * H1 * (K2 * K3 * M3 + K2 * M2 * M3);
+  }
+  double flops_cpw(PwMode mode) const {
     const int NP = (mode == PW_GT) ? 9 : 3;
     const double bflops = mode == PW_F ? 44.0 : (mode == PW_T ? 88.0 : 124.0);
+    return 4.0 * (24 + NP) * K.h1 * (double)Mvol + bflops * (double)Mvol;
+  }
+  double flops_pi_ba(int nper) const {
+    const double H1 = K.h1, K2 = K.k2, K3 = K.k3, M2 = M.n2, M3 = M.n3;
+    return 8.0 * 3 * nper * H1 * (K2 * M2 * M3 + K2 * K3 * M3);
+  }
+
+  void eval(PwMode mode, T* slot, const C* srcA, const C* srcB, const PiEpi<T>& e) {
+    if (rec) {
+      rec->push_back(EvalDesc<T>{srcA, srcB, slot, e});
+      return;
+    }
     pb(PR_IOTA_AB);
     bracket_iota<T>(pad, block24(srcA, srcB, slot), Lhat, T2, st);
-    pe(PR_IOTA_AB, 8.0 * 24 * H1 * (K2 * K3 * M3 + K2 * M2 * M3));
+    pe(PR_IOTA_AB, flops_iota_ab());
     pb(PR_CPW);
     bracket_cpw<T>(pad, mode, T2, slot, P2, st);
-    pe(PR_CPW, 4.0 * (24 + NP) * H1 * (double)Mvol + bflops * (double)Mvol);
+    pe(PR_CPW, flops_cpw(mode));
     pb(PR_PI_BA);
     bracket_pi<T>(pad, e, Lhat, P2, st);
-    pe(PR_PI_BA, 8.0 * 3 * e.nper * H1 * (K2 * M2 * M3 + K2 * K3 * M3));
+    pe(PR_PI_BA, flops_pi_ba(e.nper));
     launches += kBracketLaunches;
     check_launch("bracket evaluation");
   }
+
+  // one band-limited sweep as a single persistent cooperative kernel
+  void run_sweep(PwMode mode, const EvalDesc<T>* ev) {
+    pb(PR_SWEEP);
+    cuda(sweep_launch<T>(pad, mode, ev, 2 * Nt, Lhat, T2, P2, bar, dres + 7, st), "persistent sweep");
+    pe(PR_SWEEP, sweep_flops[mode]);
+    ++launches;
+  }
+  bool persistent() const { return opts.persistent != 0 && rec == nullptr; }
 
   // algorithmic flops of iota (or pi) of nf scalar fields on the image grid,
   // Hermitian half spectrum along axis 1
@@ -445,6 +511,10 @@ struct Impl {
 
   // Heun shoot of BL EPDiff (Eq. 51); S.vh[0] must hold v0
   void shoot(State<T>& S) {
+    if (persistent()) {
+      run_sweep(PW_F, &S == &lin ? ev_shoot_lin : ev_shoot_trial);
+      return;
+    }
     const double m = 1.0 / (double)Mvol;
     for (int n = 0; n < Nt; ++n) {
       C* vn = vec(S.vh, n);
@@ -494,15 +564,17 @@ struct Impl {
     check_launch("energy reductions");
   }
   double read_energy() {
-    cuda(cudaMemcpyAsync(hres, dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "read E");
+    cuda(cudaMemcpyAsync(hres, dres, 8 * sizeof(double), cudaMemcpyDeviceToHost, st), "read E");
     sync("energy");
+    check_flag(hres[7]);
     return 0.5 * hres[0] + hres[1] / (sigma * sigma * (double)Nvol);
   }
   double dot_V(const C* a, const C* b) {
     inner_V<T>(a, b, Lhat, 3, Kvol, partial, dres + 2, st);
     launches += 2;
-    cuda(cudaMemcpyAsync(hres + 2, dres + 2, sizeof(double), cudaMemcpyDeviceToHost, st), "read dot");
+    cuda(cudaMemcpyAsync(hres + 2, dres + 2, 6 * sizeof(double), cudaMemcpyDeviceToHost, st), "read dot");
     sync("inner product");
+    check_flag(hres[7]);
     return hres[2];
   }
 
@@ -510,7 +582,11 @@ struct Impl {
   // leaves W(0) in W
   void backward(State<T>& S) {
     const double m = 1.0 / (double)Mvol;
-    cuda(cudaMemsetAsync(W, 0, (size_t)3 * Kvol * sizeof(C), st), "memset W");
+    if (!rec) cuda(cudaMemsetAsync(W, 0, (size_t)3 * Kvol * sizeof(C), st), "memset W");
+    if (persistent()) {
+      run_sweep(PW_GT, ev_backward);
+      return;
+    }
     for (int n = Nt - 1; n >= 0; --n) {
       PiEpi<T> e1 = epi(3, 3);
       e1.grp[0] = 0; e1.coef[0] = (T)m;  e1.applyK[0] = 1;   // ad^dag_v U
@@ -533,6 +609,10 @@ struct Impl {
 
   // incremental EPDiff (Eq. 30) from dvh[0], exact tangent of the Heun shoot
   void tangent(State<T>& S) {
+    if (persistent()) {
+      run_sweep(PW_T, ev_tangent);
+      return;
+    }
     const double m = 1.0 / (double)Mvol;
     for (int n = 0; n < Nt; ++n) {
       C* dn = vec(dvh, n);
@@ -667,8 +747,18 @@ struct Impl {
       *err = "no linearisation point (call lddmm_gradient first)";
       throw Fail{LDDMM_ESTATE};
     }
+    if (opts.use_graphs && !hv_exec) {
+      try {
+        build_graph();
+      } catch (const Fail&) {
+        // capture refused (e.g. a launch kind the graph cannot hold): run the
+        // product with direct launches from now on
+        cudaGetLastError();
+        opts.use_graphs = 0;
+        err->clear();
+      }
+    }
     if (opts.use_graphs) {
-      if (!hv_exec) build_graph();
       cuda(cudaEventRecord(ev, st), "event record");
       cuda(cudaStreamWaitEvent(cap, ev, 0), "wait");
       cuda(cudaGraphLaunch(hv_exec, cap), "graph launch");
@@ -716,7 +806,9 @@ struct Impl {
     load_bl(dv, dvh);
     hessvec_dev();
     store_bl(vout, out);
+    cuda(cudaMemcpyAsync(hres + 7, dres + 7, sizeof(double), cudaMemcpyDeviceToHost, st), "read flag");
     sync("hessvec");
+    check_flag(hres[7]);
   }
 
   void gn_solve(void* v0, int n_gn, int n_pcg, lddmm_report* rep) {
@@ -878,7 +970,9 @@ struct Impl {
     load_bl(v0, trial.vh);
     shoot(trial);
     store_bl(vec(trial.vh, Nt), v1);
+    cuda(cudaMemcpyAsync(hres + 7, dres + 7, sizeof(double), cudaMemcpyDeviceToHost, st), "read flag");
     sync("shoot");
+    check_flag(hres[7]);
   }
 
   void transport_call(const void* v0, void* m1) {
@@ -887,7 +981,9 @@ struct Impl {
     forward(trial);
     cuda(cudaMemcpyAsync(m1, trial.mh + (long long)Nt * Nvol, (size_t)Nvol * sizeof(T),
                          cudaMemcpyDefault, st), "copy m1");
+    cuda(cudaMemcpyAsync(hres + 7, dres + 7, sizeof(double), cudaMemcpyDeviceToHost, st), "read flag");
     sync("transport");
+    check_flag(hres[7]);
   }
 
   void last_dm1(void* out) {
@@ -947,6 +1043,7 @@ void lddmm_default_opts(lddmm_opts* o) {
   o->armijo_c = 1e-4;
   o->max_halvings = 10;
   o->use_graphs = 1;
+  o->persistent = 1;
 }
 
 int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, double alpha, int s,

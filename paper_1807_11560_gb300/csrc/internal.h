@@ -123,6 +123,23 @@ void bracket_cpw(const Plan<T>& p, PwMode mode, const cplx<T>* T2, T* slot, cplx
 template <typename T>
 void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T>* P2,
                 cudaStream_t st);
+// One bracket evaluation of a persistent sweep: iota sources (value/Jacobian
+// block from srcA, L~ block from srcB), stage-point slot and pi epilogue.
+template <typename T>
+struct EvalDesc {
+  const cplx<T>* srcA;
+  const cplx<T>* srcB;
+  T* slot;
+  PiEpi<T> epi;
+};
+// Every evaluation of a band-limited sweep in one cooperative launch
+// (sweep.cu); ev is a device array of nev descriptors of one mode.  bar: two
+// device unsigned ints of barrier state; flag: device double set to 1 if a
+// barrier wait gave up.
+template <typename T>
+cudaError_t sweep_launch(const Plan<T>& p, PwMode mode, const EvalDesc<T>* ev, int nev, const T* Lhat,
+                         cplx<T>* T2, cplx<T>* P2, unsigned* bar, double* flag, cudaStream_t st);
+
 // largest dynamic shared memory the transform kernels need on plan p when pi
 // batches hold up to nper_max fields per component and (brackets) bracket
 // evaluations run on it; SIZE_MAX if the plan's G3 is too long for the pi

@@ -1,0 +1,169 @@
+// Persistent kernel for one whole band-limited time sweep (the Heun shoot of
+// Eq. 51, its tangent of Eq. 30, or the backward adjoint Jacobi sweep of
+// Eqs. 53-54): every bracket evaluation of the sweep runs in one cooperative
+// launch, its three phases (bracket.cuh) separated by grid-wide barriers.
+// At small grids the phases last a few microseconds each, so removing the
+// kernel boundaries between them is what bounds the sweep time.
+//
+// Barrier waits are bounded: a CTA that spins longer than the limit records
+// the failure in a flag the host reads (LDDMM_ETIMEOUT) and every CTA leaves
+// at its next barrier.  The launch is cooperative, so all CTAs are resident.
+#include "bracket.cuh"
+
+namespace lddmm {
+namespace {
+
+using dev::kThreads;
+using dev::kMaxSmem;
+
+constexpr long long kSpinLimit = 1LL << 24;   // polls of an L2 line: well over a second
+
+template <typename T>
+struct SweepArgs {
+  Plan<T> p;                  // padded product-grid plan
+  const T* Lhat;
+  cplx<T>* T2;
+  cplx<T>* P2;
+  const EvalDesc<T>* ev;      // device array of nev evaluations
+  int nev;
+  int TP;                     // pencil tile of the C/products/C' phase
+  dev::BAGeom ba;             // geometry of the pi B'/A' phase
+  unsigned* bar;              // [0] arrival counter
+  double* flag;               // set to 1 when a barrier wait gives up
+};
+
+__device__ __forceinline__ unsigned load_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier on a monotonic arrival counter (zeroed before the launch):
+// the k-th barrier of the launch completes when the counter reaches
+// k * gridDim.x.  One atomic per CTA, then acquire loads until the target.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& target, double* flag) {
+  __syncthreads();
+  target += gridDim.x;
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    long long it = 0;
+    while (load_acquire(count) < target) {
+      if (++it > kSpinLimit) {
+        *(volatile double*)flag = 1.0;
+        break;
+      }
+    }
+    if (*(volatile double*)flag != 0.0) ok = 0;
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+template <typename T, int MODE, bool TWS>
+__global__ void __launch_bounds__(kThreads)
+k_sweep(SweepArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const Plan<T>& p = a.p;
+  const int H1 = p.b.h1;
+  const long long P = (long long)p.g.n2 * p.g.n3;
+  const long long kvol = p.b.vol();
+  const int n_ab = 24 * H1;
+  const int n_cpw = (int)((P + a.TP - 1) / a.TP);
+  const int n_ba = 3 * H1 * a.ba.nch;
+  unsigned target = 0;
+  for (int ev = 0; ev < a.nev; ++ev) {
+    const EvalDesc<T>* E = a.ev + ev;
+    const cplx<T>* A = E->srcA;
+    const cplx<T>* B = E->srcB;
+    T* slot = E->slot;
+    for (int vb = blockIdx.x; vb < n_ab; vb += gridDim.x) {
+      const int f = vb / H1, h = vb % H1;
+      dev::phase_iota_ab<T, TWS>(p, dev::field24<T>(A, B, kvol, f), f, h, a.Lhat, a.T2, smraw);
+      __syncthreads();
+    }
+    if (!grid_barrier(a.bar, target, a.flag)) return;
+    for (int vb = blockIdx.x; vb < n_cpw; vb += gridDim.x) {
+      dev::phase_cpw<T, MODE>(p, a.T2, slot, a.P2, a.TP, vb, smraw);
+      __syncthreads();
+    }
+    if (!grid_barrier(a.bar, target, a.flag)) return;
+    for (int vb = blockIdx.x; vb < n_ba; vb += gridDim.x) {
+      dev::phase_pi_ba<T>(p, E->epi, a.Lhat, a.P2, a.ba, vb, smraw);
+      __syncthreads();
+    }
+    if (!grid_barrier(a.bar, target, a.flag)) return;
+  }
+}
+
+template <typename T, int MODE, bool TWS>
+cudaError_t launch(const SweepArgs<T>& a, size_t smem, cudaStream_t st, int max_ctas) {
+  auto kern = k_sweep<T, MODE, TWS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev_id = 0, sms = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaGetDevice(&dev_id)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = std::max(1, std::min(per_sm * sms, max_ctas));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <typename T, int MODE>
+cudaError_t dispatch_tws(const SweepArgs<T>& a, size_t smem, bool tws, cudaStream_t st, int max_ctas) {
+  return tws ? launch<T, MODE, true>(a, smem, st, max_ctas) : launch<T, MODE, false>(a, smem, st, max_ctas);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t sweep_launch(const Plan<T>& p, PwMode mode, const EvalDesc<T>* ev, int nev, const T* Lhat,
+                         cplx<T>* T2, cplx<T>* P2, unsigned* bar, double* flag, cudaStream_t st) {
+  SweepArgs<T> a;
+  a.p = p;
+  a.Lhat = Lhat;
+  a.T2 = T2;
+  a.P2 = P2;
+  a.ev = ev;
+  a.nev = nev;
+  a.TP = dev::cpw_tile(p);
+  const int nper = (mode == PW_GT) ? 3 : 1;
+  a.ba = dev::ba_geom(p, 3, nper);
+  a.bar = bar;
+  a.flag = flag;
+  const bool tws = dev::ab_tws(p);
+  const int NP = (mode == PW_GT) ? 9 : 3;
+  const size_t smem = std::max(dev::ab_smem(p, tws),
+                               std::max(dev::cpw_smem(p, a.TP, NP), dev::ba_smem(p, nper, a.ba)));
+  const long long P = (long long)p.g.n2 * p.g.n3;
+  const int max_ctas = (int)std::max<long long>(
+      24LL * p.b.h1, std::max<long long>((P + a.TP - 1) / a.TP, 3LL * p.b.h1 * a.ba.nch));
+  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  switch (mode) {
+    case PW_F: return dispatch_tws<T, PW_F>(a, smem, tws, st, max_ctas);
+    case PW_T: return dispatch_tws<T, PW_T>(a, smem, tws, st, max_ctas);
+    default: return dispatch_tws<T, PW_GT>(a, smem, tws, st, max_ctas);
+  }
+}
+
+template cudaError_t sweep_launch<float>(const Plan<float>&, PwMode, const EvalDesc<float>*, int,
+                                         const float*, cplx<float>*, cplx<float>*, unsigned*, double*,
+                                         cudaStream_t);
+template cudaError_t sweep_launch<double>(const Plan<double>&, PwMode, const EvalDesc<double>*, int,
+                                          const double*, cplx<double>*, cplx<double>*, unsigned*, double*,
+                                          cudaStream_t);
+
+}  // namespace lddmm

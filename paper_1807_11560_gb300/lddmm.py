@@ -30,7 +30,8 @@ class LddmmError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("pcg_tol", ctypes.c_double), ("armijo_c", ctypes.c_double),
-                ("max_halvings", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+                ("max_halvings", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("persistent", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -120,7 +121,7 @@ class Context:
     """
 
     def __init__(self, grid, K, alpha, s, sigma, Nt, precision="fp32", stream=None,
-                 use_graphs=True, pcg_tol=1e-12, armijo_c=1e-4, max_halvings=10):
+                 use_graphs=True, pcg_tol=1e-12, armijo_c=1e-4, max_halvings=10, persistent=True):
         L = lib()
         self.grid, self.K = tuple(int(g) for g in grid), tuple(int(k) for k in K)
         self.ndim = len(self.grid)
@@ -132,6 +133,7 @@ class Context:
         o.precision = LDDMM_FP64 if precision == "fp64" else LDDMM_FP32
         o.stream = stream
         o.use_graphs = 1 if use_graphs else 0
+        o.persistent = 1 if persistent else 0
         o.pcg_tol, o.armijo_c, o.max_halvings = pcg_tol, armijo_c, max_halvings
         arr = ctypes.c_int * self.ndim
         h = ctypes.c_void_p()

@@ -87,6 +87,24 @@ def test_graph_replay_equals_direct_launches():
     np.testing.assert_array_equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_persistent_sweeps_equal_per_evaluation_launches(precision):
+    """One cooperative kernel per sweep runs the same phase code as three
+    launches per bracket evaluation: the results must be bit-identical."""
+    kind, Ns, Ks, seed, Nt = CASES[2]
+    outs = []
+    for persistent in (True, False):
+        ctx, P, v0, p = problem(kind, Ns, Ks, seed, Nt, precision, persistent=persistent)
+        g = _cplx(precision, (3,) + Ks)
+        E = ctx.gradient(torch_dev(v0, precision), g)
+        Hp = _cplx(precision, (3,) + Ks)
+        ctx.hessvec(torch_dev(p, precision), Hp)
+        outs.append((E, host(g), host(Hp)))
+    assert outs[0][0] == outs[1][0]
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    np.testing.assert_array_equal(outs[0][2], outs[1][2])
+
+
 def test_host_pointers_and_state_errors():
     kind, Ns, Ks, seed, Nt = CASES[0]
     ctx, P, v0, p = problem(kind, Ns, Ks, seed, Nt, "fp32")
