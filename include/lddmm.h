@@ -83,9 +83,10 @@ typedef struct {
   double armijo_c;      /* Armijo constant; default 1e-4 */
   int max_halvings;     /* line-search halvings of eps = 1; default 10 */
   int use_graphs;       /* replay the Hessian-vector product from a CUDA graph; default 1 */
-  int persistent;       /* run each band-limited time sweep as one persistent cooperative
-                           kernel (grid barriers with bounded waits); 0 launches three
-                           kernels per bracket evaluation instead; default 1 */
+  int persistent;       /* band-limited time sweeps as one persistent cooperative kernel
+                           (grid barriers with bounded waits): 0 never (three kernels per
+                           bracket evaluation), 1 when the padded product grid has at
+                           most 32^3 points (default), 2 always */
 } lddmm_opts;
 
 /* Report of lddmm_gn_solve.  The per-iteration arrays are optional
@@ -104,13 +105,13 @@ typedef struct {
 } lddmm_report;
 
 /* Defaults for lddmm_opts (precision FP32, legacy stream, tol 1e-12,
- * c = 1e-4, 10 halvings, graphs on, persistent sweeps on). */
+ * c = 1e-4, 10 halvings, graphs on, persistent sweeps on small grids). */
 void lddmm_default_opts(lddmm_opts* opts);
 
 /* Create a registration context (Section 3.2).
  *   ndim    2 or 3.
  *   grid    ndim image sizes N_j >= 2, N_1 N_2 N_3 < 2^31 (int array, host).
- *   K       ndim band sizes: even, 2 <= K_j <= min(N_j, 512) (int array, host).
+ *   K       ndim band sizes: even, 2 <= K_j <= N_j, K_1 <= 64 (int array, host).
  *   alpha   > 0, s >= 1: L = (Id - alpha Lap)^s (Eq. 1).
  *   sigma   > 0: data weight 1/sigma^2 (Eq. 50).
  *   Nt      >= 1 time steps on [0,1].

@@ -457,7 +457,13 @@ struct Impl {
     pe(PR_SWEEP, sweep_flops[mode]);
     ++launches;
   }
-  bool persistent() const { return opts.persistent != 0 && rec == nullptr; }
+  // persistent sweeps pay off while the phases are latency-bound (small padded
+  // grids); beyond that one launch's worst-phase footprint costs occupancy
+  static constexpr long long kPersistentMaxPadded = 32768;   // M1 M2 M3
+  bool persistent() const {
+    if (rec != nullptr || opts.persistent == 0) return false;
+    return opts.persistent == 2 || Mvol <= kPersistentMaxPadded;
+  }
 
   // algorithmic flops of iota (or pi) of nf scalar fields on the image grid,
   // Hermitian half spectrum along axis 1
@@ -1053,7 +1059,7 @@ int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, doubl
   if ((ndim != 2 && ndim != 3) || !grid || !K || !(alpha > 0) || s < 1 || !(sigma > 0) || Nt < 1)
     return LDDMM_EINVAL;
   for (int j = 0; j < ndim; ++j) {
-    if (grid[j] < 2 || K[j] < 2 || (K[j] & 1) || K[j] > grid[j] || grid[j] > (1 << 16) || K[j] > 512)
+    if (grid[j] < 2 || K[j] < 2 || (K[j] & 1) || K[j] > grid[j] || grid[j] > (1 << 16) || K[j] > 512 || (j == 0 && K[j] > 64))
       return LDDMM_EINVAL;
   }
   long long nvox = 1;

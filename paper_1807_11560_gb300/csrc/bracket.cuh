@@ -23,7 +23,7 @@ namespace dev {
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr int kThreads = 256;
 constexpr int kMaxSmem = 200 * 1024;
-constexpr int kAccB = 4;      // B' accumulators per thread in phase_pi_ba
+constexpr int kAccB = 2;      // B' columns per thread in phase_pi_ba (nper * G3 <= 512)
 constexpr int kRed = 8;       // threads sharing one A' sum in phase_pi_ba
 
 __host__ __device__ __forceinline__ int sfreq(int q, int K) { return (2 * q < K) ? q : q - K; }
@@ -86,31 +86,54 @@ __device__ __forceinline__ void bracketQ(const T* a, const T* w, T* out) {
 }
 
 // ---------------------------------------------------------------------------
-// iota stages A + B of one slab.  TWS: twiddles staged in shared memory too.
+// paired loads of two consecutive complex values (16-byte aligned for float)
+template <typename C>
+__device__ __forceinline__ void ld2(const C* p, C& a, C& b) {
+  a = p[0];
+  b = p[1];
+}
+template <>
+__device__ __forceinline__ void ld2<float2>(const float2* p, float2& a, float2& b) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+
+__host__ __device__ __forceinline__ int even_up(int n) { return n + (n & 1); }
+__host__ __device__ __forceinline__ int quad_up(int n) { return (n + 3) & ~3; }
+
+// ---------------------------------------------------------------------------
+// iota stages A + B of one slab, in 2 x 2 complex register tiles.
+// Shared memory: S0 [K2][K3], S1 [K2][G3e], and with TWS the twiddles
+// E3 [K3][G3e] and E2 [K2][G2e] (G*e = even-rounded, zero padded).
 template <typename T, bool TWS>
 __device__ __forceinline__ void phase_iota_ab(const Plan<T>& p, const FieldSpec<T>& fs, int f, int h,
                                               const T* __restrict__ Lhat, cplx<T>* __restrict__ T2,
                                               unsigned char* smraw) {
   using C = cplx<T>;
   const int G2 = p.g.n2, G3 = p.g.n3, K2 = p.b.k2, K3 = p.b.k3, H1 = p.b.h1;
+  const int G2e = even_up(G2), G3e = even_up(G3);
   C* S0 = reinterpret_cast<C*>(smraw);       // [K2][K3] multiplied band slab
-  C* S1 = S0 + K2 * K3;                      // [K2][G3] after stage A
-  const C* E3 = p.E3f;
-  const C* E2 = p.E2f;
+  C* S1 = S0 + K2 * K3;                      // [K2][G3e] after stage A
+  C* E3s = S1 + K2 * G3e;                    // [K3][G3e]
+  C* E2s = E3s + K3 * G3e;                   // [K2][G2e]
   const int tid = threadIdx.x;
+  const C zero{T(0), T(0)};
   if (TWS) {
-    C* e3 = S1 + K2 * G3;                    // [K3][G3]
-    C* e2 = e3 + K3 * G3;                    // [K2][G2]
-    for (int i = tid; i < K3 * G3; i += kThreads) e3[i] = p.E3f[i];
-    for (int i = tid; i < K2 * G2; i += kThreads) e2[i] = p.E2f[i];
-    E3 = e3;
-    E2 = e2;
+    for (int i = tid; i < K3 * G3e; i += kThreads) {
+      const int r = i / G3e, x = i - r * G3e;
+      E3s[i] = x < G3 ? p.E3f[r * G3 + x] : zero;
+    }
+    for (int i = tid; i < K2 * G2e; i += kThreads) {
+      const int r = i / G2e, x = i - r * G2e;
+      E2s[i] = x < G2 ? p.E2f[r * G2 + x] : zero;
+    }
   }
   const C* __restrict__ src = fs.src + (long long)h * K2 * K3;
   const T* __restrict__ Lrow = Lhat + (long long)h * K2 * K3;
   for (int i = tid; i < K2 * K3; i += kThreads) {
-    const int k2 = i / K3, k3 = i % K3;
-    C a{T(0), T(0)};
+    const int k2 = i / K3, k3 = i - k2 * K3;
+    C a = zero;
     if (!nyq(k2, K2) && !nyq(k3, K3)) {
       a = src[i];
       if (fs.applyL) { const T l = Lrow[i]; a.x *= l; a.y *= l; }
@@ -125,25 +148,61 @@ __device__ __forceinline__ void phase_iota_ab(const Plan<T>& p, const FieldSpec<
     S0[i] = a;
   }
   __syncthreads();
-  for (int it = tid; it < K2 * G3; it += kThreads) {            // A: k3 -> x3
-    const int k2 = it / G3, x3 = it % G3;
-    C acc{T(0), T(0)};
+  // A: S1[k2][x3] = sum_k3 S0[k2][k3] E3[k3][x3]   (K2 is even)
+  const int n3p = G3e / 2;
+  for (int it = tid; it < (K2 / 2) * n3p; it += kThreads) {
+    const int kp = it / n3p, xp = it - kp * n3p;
+    const int k2 = 2 * kp, x3 = 2 * xp;
+    C c00 = zero, c01 = zero, c10 = zero, c11 = zero;
     const C* s0 = S0 + k2 * K3;
-    for (int k3 = 0; k3 < K3; ++k3) cmac(acc, s0[k3], E3[k3 * G3 + x3]);
-    S1[it] = acc;
+    for (int k3 = 0; k3 < K3; ++k3) {
+      const C a0 = s0[k3], a1 = s0[K3 + k3];
+      C e0, e1;
+      if (TWS) {
+        ld2(E3s + k3 * G3e + x3, e0, e1);
+      } else {
+        e0 = p.E3f[k3 * G3 + x3];
+        e1 = x3 + 1 < G3 ? p.E3f[k3 * G3 + x3 + 1] : zero;
+      }
+      cmac(c00, a0, e0); cmac(c01, a0, e1); cmac(c10, a1, e0); cmac(c11, a1, e1);
+    }
+    S1[k2 * G3e + x3] = c00;
+    S1[k2 * G3e + x3 + 1] = c01;
+    S1[(k2 + 1) * G3e + x3] = c10;
+    S1[(k2 + 1) * G3e + x3 + 1] = c11;
   }
   __syncthreads();
+  // B: out[x2][x3] = sum_k2 E2[k2][x2] S1[k2][x3]
   C* __restrict__ out = T2 + (long long)(f * H1 + h) * G2 * G3;
-  for (int it = tid; it < G2 * G3; it += kThreads) {            // B: k2 -> x2
-    const int x2 = it / G3, x3 = it % G3;
-    C acc{T(0), T(0)};
-    for (int k2 = 0; k2 < K2; ++k2) cmac(acc, S1[k2 * G3 + x3], E2[k2 * G2 + x2]);
-    out[it] = acc;
+  const int n2p = G2e / 2;
+  for (int it = tid; it < n2p * n3p; it += kThreads) {
+    const int yp = it / n3p, xp = it - yp * n3p;
+    const int x2 = 2 * yp, x3 = 2 * xp;
+    C c00 = zero, c01 = zero, c10 = zero, c11 = zero;
+    for (int k2 = 0; k2 < K2; ++k2) {
+      C s0, s1, e0, e1;
+      ld2(S1 + k2 * G3e + x3, s0, s1);
+      if (TWS) {
+        ld2(E2s + k2 * G2e + x2, e0, e1);
+      } else {
+        e0 = p.E2f[k2 * G2 + x2];
+        e1 = x2 + 1 < G2 ? p.E2f[k2 * G2 + x2 + 1] : zero;
+      }
+      cmac(c00, s0, e0); cmac(c01, s1, e0); cmac(c10, s0, e1); cmac(c11, s1, e1);
+    }
+    out[(long long)x2 * G3 + x3] = c00;
+    if (x3 + 1 < G3) out[(long long)x2 * G3 + x3 + 1] = c01;
+    if (x2 + 1 < G2) {
+      out[(long long)(x2 + 1) * G3 + x3] = c10;
+      if (x3 + 1 < G3) out[(long long)(x2 + 1) * G3 + x3 + 1] = c11;
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // C + bracket products + C' on one tile of TP pencils, all G1 planes.
+// Twiddles staged zero-padded: E1f [H1][G1q] and E1b [G1][H1q] (q = rounded
+// up to 4), so C works on 4 planes and C' on 4 band slots per thread.
 template <typename T, int MODE>
 __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __restrict__ T2,
                                           T* __restrict__ slot, cplx<T>* __restrict__ P2, int TP, int vb,
@@ -151,40 +210,64 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
   using C = cplx<T>;
   constexpr int NP = (MODE == PW_GT) ? 9 : 3;
   const int G1 = p.g.n1, H1 = p.b.h1;
+  const int G1q = quad_up(G1), H1q = quad_up(H1);
   const long long P = (long long)p.g.n2 * p.g.n3;
   C* sT2 = reinterpret_cast<C*>(smraw);                    // [24][H1][TP]
-  C* sE1f = sT2 + 24 * H1 * TP;                            // [H1][G1]
-  C* sE1b = sE1f + H1 * G1;                                // [G1][H1]
-  T* sG = reinterpret_cast<T*>(sE1b + G1 * H1);            // [24][G1][TP]
+  C* sE1f = sT2 + 24 * H1 * TP;                            // [H1][G1q]
+  C* sE1b = sE1f + H1 * G1q;                               // [G1][H1q]
+  T* sG = reinterpret_cast<T*>(sE1b + G1 * H1q);           // [24][G1][TP]
   T* sP = sG + 24 * G1 * TP;                               // [NP][G1][TP]
   const int tid = threadIdx.x;
   const long long p0 = (long long)vb * TP;
+  const C zero{T(0), T(0)};
 
-  for (int i = tid; i < 24 * H1 * TP; i += kThreads) {
-    const int pp = i % TP, fh = i / TP;                     // fh = f * H1 + h
-    sT2[i] = (p0 + pp < P) ? T2[(long long)fh * P + p0 + pp] : C{T(0), T(0)};
+  for (int fh = tid / TP, pp = tid - (tid / TP) * TP; fh < 24 * H1;) {
+    sT2[fh * TP + pp] = (p0 + pp < P) ? T2[(long long)fh * P + p0 + pp] : zero;
+    pp += kThreads % TP;
+    fh += kThreads / TP;
+    if (pp >= TP) { pp -= TP; ++fh; }
   }
-  for (int i = tid; i < H1 * G1; i += kThreads) {
-    sE1f[i] = p.E1f[i];
-    sE1b[i] = p.E1b[i];
+  for (int i = tid; i < H1 * G1q; i += kThreads) {
+    const int h = i / G1q, x = i - h * G1q;
+    sE1f[i] = x < G1 ? p.E1f[h * G1 + x] : zero;
+  }
+  for (int i = tid; i < G1 * H1q; i += kThreads) {
+    const int x = i / H1q, h = i - x * H1q;
+    sE1b[i] = h < H1 ? p.E1b[x * H1 + h] : zero;
   }
   __syncthreads();
   const long long fs = (long long)G1 * P;                  // field stride of a slot
-  for (int i = tid; i < 24 * G1 * TP; i += kThreads) {     // C: 24 grid fields
-    const int pp = i % TP, x1 = (i / TP) % G1, f = i / (TP * G1);
+  const int nq = G1q / 4;
+  for (int it = tid; it < 24 * TP * nq; it += kThreads) {  // C: 24 grid fields, 4 planes each
+    const int f = it / (TP * nq);                          // pencil fastest: the sT2 reads are
+    const int rem = it - f * TP * nq;                      // consecutive and the twiddle reads
+    const int xq = rem / TP, pp = rem - xq * TP;           // broadcast
+    const int x0 = 4 * xq;
     const C* s = sT2 + f * H1 * TP + pp;
-    T v = T(0);
+    T v0 = T(0), v1 = T(0), v2 = T(0), v3 = T(0);
     for (int h = 0; h < H1; ++h) {
-      const C e = sE1f[h * G1 + x1];
       const C a = s[h * TP];
-      v = fma(a.x, e.x, fma(-a.y, e.y, v));
+      C e0, e1, e2, e3;
+      ld2(sE1f + h * G1q + x0, e0, e1);
+      ld2(sE1f + h * G1q + x0 + 2, e2, e3);
+      v0 = fma(a.x, e0.x, fma(-a.y, e0.y, v0));
+      v1 = fma(a.x, e1.x, fma(-a.y, e1.y, v1));
+      v2 = fma(a.x, e2.x, fma(-a.y, e2.y, v2));
+      v3 = fma(a.x, e3.x, fma(-a.y, e3.y, v3));
     }
-    sG[i] = v;
-    if (MODE == PW_F && p0 + pp < P) slot[f * fs + (long long)x1 * P + p0 + pp] = v;
+    const T vv[4] = {v0, v1, v2, v3};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int x1 = x0 + t;
+      if (x1 < G1) {
+        sG[(f * G1 + x1) * TP + pp] = vv[t];
+        if (MODE == PW_F && p0 + pp < P) slot[f * fs + (long long)x1 * P + p0 + pp] = vv[t];
+      }
+    }
   }
   __syncthreads();
   for (int i = tid; i < G1 * TP; i += kThreads) {          // bracket products
-    const int pp = i % TP, x1 = i / TP;
+    const int x1 = i / TP, pp = i - x1 * TP;
     T o[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) o[q] = T(0);
@@ -219,26 +302,39 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
     for (int q = 0; q < NP; ++q) sP[q * G1 * TP + i] = o[q];
   }
   __syncthreads();
-  for (int i = tid; i < NP * H1 * TP; i += kThreads) {     // C': x1 -> h
-    const int pp = i % TP, h = (i / TP) % H1, q = i / (TP * H1);
+  const int nh = H1q / 4;
+  for (int it = tid; it < NP * TP * nh; it += kThreads) {  // C': x1 -> h, 4 slots each
+    const int q = it / (TP * nh);
+    const int rem = it - q * TP * nh;
+    const int hq = rem / TP, pp = rem - hq * TP;
+    const int h0 = 4 * hq;
     if (p0 + pp >= P) continue;
     const T* sp = sP + q * G1 * TP + pp;
-    C acc{T(0), T(0)};
+    C a0 = zero, a1 = zero, a2 = zero, a3 = zero;
     for (int x1 = 0; x1 < G1; ++x1) {
       const T v = sp[x1 * TP];
-      const C e = sE1b[x1 * H1 + h];
-      acc.x = fma(v, e.x, acc.x);
-      acc.y = fma(v, e.y, acc.y);
+      C e0, e1, e2, e3;
+      ld2(sE1b + x1 * H1q + h0, e0, e1);
+      ld2(sE1b + x1 * H1q + h0 + 2, e2, e3);
+      a0.x = fma(v, e0.x, a0.x); a0.y = fma(v, e0.y, a0.y);
+      a1.x = fma(v, e1.x, a1.x); a1.y = fma(v, e1.y, a1.y);
+      a2.x = fma(v, e2.x, a2.x); a2.y = fma(v, e2.y, a2.y);
+      a3.x = fma(v, e3.x, a3.x); a3.y = fma(v, e3.y, a3.y);
     }
-    P2[(long long)(q * H1 + h) * P + p0 + pp] = acc;
+    const C aa[4] = {a0, a1, a2, a3};
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (h0 + t < H1) P2[(long long)(q * H1 + h0 + t) * P + p0 + pp] = aa[t];
   }
 }
 
 // ---------------------------------------------------------------------------
-// pi B' + A' + epilogue for (component c, h, k2 chunk).  B' streams the P2
-// slab of every product field of c in chunks of XB rows of x2 through shared
-// memory, each thread keeping up to kAccB accumulators of S1[o][kk][x3]; A'
-// splits every band-slot sum over kRed threads and reduces with shuffles.
+// pi B' + A' + epilogue for (component c, h, k2 chunk of kc <= kMaxKC rows).
+// B' streams the P2 slab of every product field of c in chunks of XB rows of
+// x2 through shared memory; a thread owns up to kAccB (field, x3) columns and
+// accumulates all kc rows of each.  A' splits every band-slot sum over kRed
+// lanes and reduces with shuffles.
+constexpr int kMaxKC = 8;
 struct BAGeom {
   int KC, nch, XB;
 };
@@ -255,7 +351,7 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
   const int nper = e.nper, ncomp = e.ncomp, nout = e.nout;
   C* slab = reinterpret_cast<C*>(smraw);                   // [nper][XB][G3]
   C* E2s = slab + nper * XB * G3;                          // [G2][KC]
-  C* E3s = E2s + G2 * KC;                                  // [G3][K3]
+  C* E3s = E2s + G2 * KC;                                  // [K3][G3] (transposed E3b)
   C* S1 = E3s + G3 * K3;                                   // [nper][KC][G3]
   const int chunk = vb % nch;
   const int h = (vb / nch) % H1;
@@ -263,41 +359,55 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
   const int kb = chunk * KC;
   const int kc = min(KC, K2 - kb);
   const int tid = threadIdx.x;
+  const C zero{T(0), T(0)};
 
   for (int i = tid; i < G2 * KC; i += kThreads) {
-    const int x2 = i / KC, kk = i % KC;
-    E2s[i] = kk < kc ? p.E2b[(long long)x2 * K2 + kb + kk] : C{T(0), T(0)};
+    const int x2 = i / KC, kk = i - x2 * KC;
+    E2s[i] = kk < kc ? p.E2b[(long long)x2 * K2 + kb + kk] : zero;
   }
-  for (int i = tid; i < G3 * K3; i += kThreads) E3s[i] = p.E3b[i];
-  C acc[kAccB];
+  for (int i = tid; i < G3 * K3; i += kThreads) {
+    const int x = i / K3, k = i - x * K3;
+    E3s[k * G3 + x] = p.E3b[i];
+  }
+  C acc[kAccB][kMaxKC];
 #pragma unroll
-  for (int r = 0; r < kAccB; ++r) acc[r] = C{T(0), T(0)};
-  const int nitem = nper * kc * G3;
+  for (int r = 0; r < kAccB; ++r)
+#pragma unroll
+    for (int kk = 0; kk < kMaxKC; ++kk) acc[r][kk] = zero;
+  const int ncol = nper * G3;
   for (int x2c = 0; x2c < G2; x2c += XB) {
     const int xb = min(XB, G2 - x2c);
     if (x2c > 0) __syncthreads();
-    for (int i = tid; i < nper * xb * G3; i += kThreads) {
-      const int x3 = i % G3, xr = (i / G3) % xb, o = i / (G3 * xb);
-      const int f = o * ncomp + c;
-      slab[(o * XB + xr) * G3 + x3] = P2[(long long)(f * H1 + h) * P + (long long)(x2c + xr) * G3 + x3];
+    for (int o = 0; o < nper; ++o) {
+      const C* __restrict__ src = P2 + (long long)((o * ncomp + c) * H1 + h) * P + (long long)x2c * G3;
+      C* dst = slab + o * XB * G3;
+      for (int i = tid; i < xb * G3; i += kThreads) dst[i] = src[i];
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kAccB; ++r) {
-      const int it = tid + r * kThreads;
-      if (it < nitem) {
-        const int x3 = it % G3, kk = (it / G3) % kc, o = it / (G3 * kc);
+      const int col = tid + r * kThreads;
+      if (col < ncol) {
+        const int o = col / G3, x3 = col - o * G3;
         const C* sl = slab + o * XB * G3 + x3;
-        for (int xr = 0; xr < xb; ++xr) cmac(acc[r], sl[xr * G3], E2s[(x2c + xr) * KC + kk]);
+        for (int xr = 0; xr < xb; ++xr) {
+          const C a = sl[xr * G3];
+          const C* er = E2s + (x2c + xr) * KC;
+#pragma unroll
+          for (int kk = 0; kk < kMaxKC; ++kk)
+            if (kk < kc) cmac(acc[r][kk], a, er[kk]);
+        }
       }
     }
   }
 #pragma unroll
   for (int r = 0; r < kAccB; ++r) {
-    const int it = tid + r * kThreads;
-    if (it < nitem) {
-      const int x3 = it % G3, kk = (it / G3) % kc, o = it / (G3 * kc);
-      S1[(o * KC + kk) * G3 + x3] = acc[r];
+    const int col = tid + r * kThreads;
+    if (col < ncol) {
+      const int o = col / G3, x3 = col - o * G3;
+#pragma unroll
+      for (int kk = 0; kk < kMaxKC; ++kk)
+        if (kk < kc) S1[(o * KC + kk) * G3 + x3] = acc[r][kk];
     }
   }
   __syncthreads();
@@ -308,15 +418,17 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
     const int lin = base + tid;
     const int it = lin / kRed, part = lin % kRed;
     const bool live = it < nslot;
-    const int k3 = live ? it % K3 : 0, kk = live ? it / K3 : 0;
+    const int kk = live ? it / K3 : 0;
+    const int k3 = live ? it - kk * K3 : 0;
     const int k2 = kb + kk;
     const bool nq = !live || nyq(k2, K2) || nyq(k3, K3);
-    C R[2] = {C{T(0), T(0)}, C{T(0), T(0)}};
+    C R[2] = {zero, zero};
     for (int o = 0; o < nper; ++o) {
-      C y{T(0), T(0)};
+      C y = zero;
       if (!nq) {
         const C* row = S1 + (o * KC + kk) * G3;
-        for (int x = part; x < G3; x += kRed) cmac(y, row[x], E3s[x * K3 + k3]);
+        const C* er = E3s + k3 * G3;
+        for (int x = part; x < G3; x += kRed) cmac(y, row[x], er[x]);
       }
 #pragma unroll
       for (int off = kRed / 2; off > 0; off >>= 1) {
@@ -336,7 +448,7 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
     // read every X term before any write: outputs may alias inputs
     C val[kMaxOut];
     for (int j = 0; j < nout; ++j) {
-      C v{T(0), T(0)};
+      C v = zero;
       if (!nq) {
         if (e.r[j] >= 0) { v.x = e.cR[j] * R[e.r[j]].x; v.y = e.cR[j] * R[e.r[j]].y; }
         for (int q = 0; q < e.nx[j]; ++q) {
@@ -353,7 +465,7 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
     for (int j = 0; j < nout; ++j) {
       e.dst[j][at] = val[j];
       if (h > 0) e.dst[j][mir] = C{val[j].x, -val[j].y};
-      if (h == 0 && K1 % 2 == 0) e.dst[j][nyq1] = C{T(0), T(0)};
+      if (h == 0 && K1 % 2 == 0) e.dst[j][nyq1] = zero;
     }
   }
 }
@@ -362,20 +474,21 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
 // launch geometry (host and device)
 template <typename T>
 __host__ __device__ inline size_t ab_smem(const Plan<T>& p, bool tws) {
-  size_t n = (size_t)p.b.k2 * p.b.k3 + (size_t)p.b.k2 * p.g.n3;
-  if (tws) n += (size_t)p.b.k3 * p.g.n3 + (size_t)p.b.k2 * p.g.n2;
+  const size_t G2e = even_up(p.g.n2), G3e = even_up(p.g.n3);
+  size_t n = (size_t)p.b.k2 * p.b.k3 + (size_t)p.b.k2 * G3e;
+  if (tws) n += (size_t)p.b.k3 * G3e + (size_t)p.b.k2 * G2e;
   return n * sizeof(cplx<T>);
 }
 
 template <typename T>
 __host__ __device__ inline bool ab_tws(const Plan<T>& p) {
-  return ab_smem(p, true) <= 64 * 1024;
+  return ab_smem(p, true) <= (size_t)kMaxSmem;
 }
 
 template <typename T>
 __host__ __device__ inline size_t cpw_smem(const Plan<T>& p, int TP, int NP) {
   const int G1 = p.g.n1, H1 = p.b.h1;
-  return ((size_t)24 * H1 * TP + 2 * (size_t)H1 * G1) * sizeof(cplx<T>) +
+  return ((size_t)24 * H1 * TP + (size_t)H1 * quad_up(G1) + (size_t)G1 * quad_up(H1)) * sizeof(cplx<T>) +
          (size_t)(24 + NP) * G1 * TP * sizeof(T);
 }
 
@@ -393,8 +506,7 @@ inline BAGeom ba_geom(const Plan<T>& p, int ncomp, int nper) {
   const int groups = ncomp * p.b.h1;
   const int want = std::max(1, (304 + groups - 1) / groups);
   int KC = std::max(1, (K2 + want - 1) / want);
-  KC = std::max(1, std::min(KC, (kAccB * kThreads) / std::max(1, nper * G3)));
-  KC = std::min(KC, K2);
+  KC = std::min(std::min(KC, kMaxKC), K2);
   const int nch = (K2 + KC - 1) / KC;
   const size_t c = sizeof(cplx<T>);
   const size_t fixed = ((size_t)G2 * KC + (size_t)G3 * K3 + (size_t)nper * KC * G3) * c;

@@ -16,10 +16,12 @@
 //
 // Kernels (CTAs of 256 threads; bodies in bracket.cuh):
 //   k_iota_AB  CTA per (field, h): A and B through shared memory -> T2.
-//   k_iota_C   thread per output, C -> grid field (image-grid transforms).
+//   k_iota_C   CTA per (field, 256 pencils): C -> grid field (image-grid
+//              transforms); each pencil's K1/2 coefficients read once.
 //   k_cpw      CTA per tile of (x2,x3) pencils: C of the 24 fields of a
 //              bracket evaluation, the bracket products, C' -> P2.
-//   k_pi_C     thread per output, C' of image-grid fields -> P2.
+//   k_pi_C     CTA per (field, 256 pencils): C' of image-grid fields -> P2,
+//              each pencil streamed once.
 //   k_pi_BA    CTA per (component, h, k2 chunk): B', A', epilogue.
 #include "bracket.cuh"
 
@@ -29,7 +31,6 @@ namespace {
 using dev::kThreads;
 using dev::kMaxSmem;
 
-inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 template <auto Kernel>
 void allow_smem() {
@@ -64,72 +65,80 @@ k_pi_BA(Plan<T> p, PiEpi<T> e, const T* __restrict__ Lhat, const cplx<T>* __rest
 }
 
 // ---- iota C: half-spectrum k1 -> x1, real output ----------------------------------
-template <typename T, int YT>
+// CTA per (field, 256 consecutive (x2,x3) positions): every thread loads the
+// H1 complex values of its position once into registers and walks all x1,
+// the twiddle row E1f[.][x1] broadcast from shared memory.
+constexpr int kMaxH1Reg = 32;
+template <typename T, int HR>
 __global__ void __launch_bounds__(kThreads)
 k_iota_C(Plan<T> p, IotaDesc<T> d, const cplx<T>* __restrict__ T2) {
   using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sE = reinterpret_cast<C*>(smraw);                     // [G1][H1] = E1f transposed
   const int G1 = p.g.n1, H1 = p.b.h1;
   const long long inner = (long long)p.g.n2 * p.g.n3;
-  const int nyt = (G1 + YT - 1) / YT;
-  const long long total = (long long)d.nf * nyt * inner;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const long long i = idx % inner;
-  long long r = idx / inner;
-  const int ty = (int)(r % nyt);
-  const int f = (int)(r / nyt);
-  const int y0 = ty * YT;
-  T acc[YT];
-#pragma unroll
-  for (int t = 0; t < YT; ++t) acc[t] = T(0);
-  const C* __restrict__ src = T2 + (long long)f * H1 * inner + i;
-  for (int h = 0; h < H1; ++h) {
-    const C a = src[(long long)h * inner];
-    const C* __restrict__ Eh = p.E1f + (long long)h * G1 + y0;
-#pragma unroll
-    for (int t = 0; t < YT; ++t)
-      if (y0 + t < G1) acc[t] = fma(a.x, Eh[t].x, fma(-a.y, Eh[t].y, acc[t]));
+  const long long nblk = (inner + kThreads - 1) / kThreads;
+  const int f = (int)(blockIdx.x / nblk);
+  const long long i = (blockIdx.x % nblk) * kThreads + threadIdx.x;
+  for (int j = threadIdx.x; j < H1 * G1; j += kThreads) {   // written in shared-memory order
+    const int x = j / H1, h = j - x * H1;
+    sE[j] = p.E1f[h * G1 + x];
   }
-  T* dst = d.dst[f] + (long long)y0 * inner + i;
+  C a[HR];
+  const bool live = i < inner;
+  const C* __restrict__ src = T2 + (long long)f * H1 * inner + i;
 #pragma unroll
-  for (int t = 0; t < YT; ++t)
-    if (y0 + t < G1) dst[(long long)t * inner] = acc[t];
+  for (int h = 0; h < HR; ++h) a[h] = (live && h < H1) ? src[(long long)h * inner] : C{T(0), T(0)};
+  __syncthreads();
+  if (!live) return;
+  T* __restrict__ dst = d.dst[f] + i;
+  for (int x = 0; x < G1; ++x) {
+    const C* e = sE + x * H1;
+    T v0 = T(0), v1 = T(0);
+#pragma unroll
+    for (int h = 0; h < HR; h += 2) {
+      if (h < H1) v0 = fma(a[h].x, e[h].x, fma(-a[h].y, e[h].y, v0));
+      if (h + 1 < H1) v1 = fma(a[h + 1].x, e[h + 1].x, fma(-a[h + 1].y, e[h + 1].y, v1));
+    }
+    dst[(long long)x * inner] = v0 + v1;
+  }
 }
 
 // ---- pi C': real grid x1 -> half-spectrum h ----------------------------------------
-template <typename T, int YT>
+// CTA per (field, 256 consecutive positions): each thread streams its pencil
+// over x1 once (coalesced) and keeps the H1 complex sums in registers.
+template <typename T, int HR>
 __global__ void __launch_bounds__(kThreads)
 k_pi_C(Plan<T> p, PiSrc<T> s, cplx<T>* __restrict__ P2) {
   using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sE = reinterpret_cast<C*>(smraw);                     // [G1][H1] = E1b
   const int G1 = p.g.n1, H1 = p.b.h1;
   const long long inner = (long long)p.g.n2 * p.g.n3;
-  const int nyt = (H1 + YT - 1) / YT;
-  const long long total = (long long)s.nf * nyt * inner;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const long long i = idx % inner;
-  long long r = idx / inner;
-  const int ty = (int)(r % nyt);
-  const int f = (int)(r / nyt);
-  const int y0 = ty * YT;
-  C acc[YT];
+  const long long nblk = (inner + kThreads - 1) / kThreads;
+  const int f = (int)(blockIdx.x / nblk);
+  const long long i = (blockIdx.x % nblk) * kThreads + threadIdx.x;
+  for (int j = threadIdx.x; j < H1 * G1; j += kThreads) sE[j] = p.E1b[j];
+  __syncthreads();
+  if (i >= inner) return;
+  C acc[HR];
 #pragma unroll
-  for (int t = 0; t < YT; ++t) acc[t] = C{T(0), T(0)};
+  for (int h = 0; h < HR; ++h) acc[h] = C{T(0), T(0)};
   const T* __restrict__ src = s.src[f] + i;
   for (int x = 0; x < G1; ++x) {
-    const T a = src[(long long)x * inner];
-    const C* __restrict__ Ex = p.E1b + (long long)x * H1 + y0;
+    const T v = src[(long long)x * inner];
+    const C* e = sE + x * H1;
 #pragma unroll
-    for (int t = 0; t < YT; ++t)
-      if (y0 + t < H1) {
-        acc[t].x = fma(a, Ex[t].x, acc[t].x);
-        acc[t].y = fma(a, Ex[t].y, acc[t].y);
+    for (int h = 0; h < HR; ++h)
+      if (h < H1) {
+        acc[h].x = fma(v, e[h].x, acc[h].x);
+        acc[h].y = fma(v, e[h].y, acc[h].y);
       }
   }
-  C* dst = P2 + ((long long)f * H1 + y0) * inner + i;
+  C* dst = P2 + (long long)f * H1 * inner + i;
 #pragma unroll
-  for (int t = 0; t < YT; ++t)
-    if (y0 + t < H1) dst[(long long)t * inner] = acc[t];
+  for (int h = 0; h < HR; ++h)
+    if (h < H1) dst[(long long)h * inner] = acc[h];
 }
 
 template <typename T>
@@ -154,8 +163,11 @@ void launch_pi_BA(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx
 
 template <typename T>
 size_t max_smem_needed(const Plan<T>& p, int nper_max, bool brackets) {
-  // every B' item of a CTA needs its own accumulator
+  // every B' column of a CTA needs its own accumulators, and the image-grid
+  // C/C' kernels keep the K1/2 slots of a pencil in registers
   if ((long long)nper_max * p.g.n3 > (long long)dev::kAccB * kThreads) return ~size_t(0);
+  if (p.b.h1 > kMaxH1Reg) return ~size_t(0);
+  if ((size_t)p.b.h1 * p.g.n1 * sizeof(cplx<T>) > (size_t)kMaxSmem) return ~size_t(0);
   const size_t ab = dev::ab_smem(p, dev::ab_tws(p));
   const size_t cpw = brackets ? dev::cpw_smem(p, dev::cpw_tile(p), 9) : 0;
   size_t ba = 0;
@@ -166,20 +178,39 @@ size_t max_smem_needed(const Plan<T>& p, int nper_max, bool brackets) {
 
 size_t smem_limit() { return kMaxSmem; }
 
+// register slots of the image-grid C / C' kernels: the smallest of 8/16/32 >= K1/2
+template <typename T, int HR>
+void launch_C(const Plan<T>& p, const IotaDesc<T>& d, const cplx<T>* T2, unsigned grid, size_t smem,
+              cudaStream_t st) {
+  allow_smem<k_iota_C<T, HR>>();
+  k_iota_C<T, HR><<<grid, kThreads, smem, st>>>(p, d, T2);
+}
+template <typename T, int HR>
+void launch_Cb(const Plan<T>& p, const PiSrc<T>& s, cplx<T>* P2, unsigned grid, size_t smem, cudaStream_t st) {
+  allow_smem<k_pi_C<T, HR>>();
+  k_pi_C<T, HR><<<grid, kThreads, smem, st>>>(p, s, P2);
+}
+
 template <typename T>
 void iota_batch(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2, cudaStream_t st) {
-  constexpr int YT = 4;
   launch_iota_AB<T>(p, d, Lhat, T2, st);
-  const long long nC = (long long)d.nf * ((p.g.n1 + YT - 1) / YT) * p.g.n2 * p.g.n3;
-  k_iota_C<T, YT><<<blocks_for(nC), kThreads, 0, st>>>(p, d, T2);
+  const long long nblk = ((long long)p.g.n2 * p.g.n3 + kThreads - 1) / kThreads;
+  const size_t smem = (size_t)p.b.h1 * p.g.n1 * sizeof(cplx<T>);
+  const unsigned grid = (unsigned)(d.nf * nblk);
+  if (p.b.h1 <= 8) launch_C<T, 8>(p, d, T2, grid, smem, st);
+  else if (p.b.h1 <= 16) launch_C<T, 16>(p, d, T2, grid, smem, st);
+  else launch_C<T, 32>(p, d, T2, grid, smem, st);
 }
 
 template <typename T>
 void pi_batch(const Plan<T>& p, const PiSrc<T>& s, const PiEpi<T>& e, const T* Lhat, cplx<T>* P2,
               cudaStream_t st) {
-  constexpr int YT = 4;
-  const long long nC = (long long)s.nf * ((p.b.h1 + YT - 1) / YT) * p.g.n2 * p.g.n3;
-  k_pi_C<T, YT><<<blocks_for(nC), kThreads, 0, st>>>(p, s, P2);
+  const long long nblk = ((long long)p.g.n2 * p.g.n3 + kThreads - 1) / kThreads;
+  const size_t smem = (size_t)p.b.h1 * p.g.n1 * sizeof(cplx<T>);
+  const unsigned grid = (unsigned)(s.nf * nblk);
+  if (p.b.h1 <= 8) launch_Cb<T, 8>(p, s, P2, grid, smem, st);
+  else if (p.b.h1 <= 16) launch_Cb<T, 16>(p, s, P2, grid, smem, st);
+  else launch_Cb<T, 32>(p, s, P2, grid, smem, st);
   launch_pi_BA<T>(p, e, Lhat, P2, st);
 }
 

@@ -121,7 +121,7 @@ class Context:
     """
 
     def __init__(self, grid, K, alpha, s, sigma, Nt, precision="fp32", stream=None,
-                 use_graphs=True, pcg_tol=1e-12, armijo_c=1e-4, max_halvings=10, persistent=True):
+                 use_graphs=True, pcg_tol=1e-12, armijo_c=1e-4, max_halvings=10, persistent="auto"):
         L = lib()
         self.grid, self.K = tuple(int(g) for g in grid), tuple(int(k) for k in K)
         self.ndim = len(self.grid)
@@ -133,7 +133,7 @@ class Context:
         o.precision = LDDMM_FP64 if precision == "fp64" else LDDMM_FP32
         o.stream = stream
         o.use_graphs = 1 if use_graphs else 0
-        o.persistent = 1 if persistent else 0
+        o.persistent = {True: 2, False: 0, "auto": 1}[persistent]
         o.pcg_tol, o.armijo_c, o.max_halvings = pcg_tol, armijo_c, max_halvings
         arr = ctypes.c_int * self.ndim
         h = ctypes.c_void_p()
