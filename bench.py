@@ -166,6 +166,25 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- ranks
+def rank_seed(seed, rank):
+    """Each rank registers its own pair (replicas, no data-path collective)."""
+    return seed + 1000 * rank
+
+
+def combine_ranks(t_sec, n_hv, world, device):
+    """Whole-job figures: the slowest rank's time and the products of all ranks."""
+    if world == 1:
+        return float(t_sec), float(n_hv)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_sec)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(n_hv)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 # --------------------------------------------------------------------------- GPU arm
 PROBE_CLASSES = ("sweep", "iota_ab", "cpw", "pi_ba", "inc_step", "transport", "iota_full", "pi_full")
 HBM_CLASSES = ("inc_step", "transport")
@@ -202,7 +221,7 @@ def run_gpu(args):
     name = args.workload
     kind, Ns, Ks, Nt, seed = workload(name)
     d = len(Ns)
-    I0, I1 = inputs.make_pair(kind, Ns, seed + 1000 * rank)
+    I0, I1 = inputs.make_pair(kind, Ns, rank_seed(seed, rank))
     I0d = torch.as_tensor(I0, dtype=torch.float32, device=dev)
     I1d = torch.as_tensor(I1, dtype=torch.float32, device=dev)
     ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision="fp32")
@@ -261,14 +280,7 @@ def run_gpu(args):
     probe_ms, probe_n, probe_work = ctx.probe_read()
     ctx.probe(None)
 
-    tt = torch.tensor([t_dev, float(hv)], dtype=torch.float64, device=dev)
-    if world > 1:
-        tmax = tt.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tmax[1:2], op=dist.ReduceOp.SUM)
-        t_dev, hv_all = float(tmax[0]), float(tmax[1])
-    else:
-        hv_all = float(hv)
+    t_dev, hv_all = combine_ranks(t_dev, hv, world, dev)
     value = hv_all / t_dev
 
     # pure Hessian-vector rate at a fixed linearisation point (context figure)
@@ -302,11 +314,7 @@ def run_gpu(args):
         hv_e2e += rep["pcg_iters"]
     barrier()
     te = time.perf_counter() - te0
-    if world > 1:
-        tt = torch.tensor([te, float(hv_e2e)], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:2], op=dist.ReduceOp.SUM)
-        te, hv_e2e = float(tt[0]), float(tt[1])
+    te, hv_e2e = combine_ranks(te, hv_e2e, world, dev)
     e2e_value = hv_e2e / te
 
     if rank == 0:

@@ -211,6 +211,18 @@ int lddmm_shoot(lddmm_ctx* ctx, const void* v0, void* v1_out);
  * the linearisation point. */
 int lddmm_transport(lddmm_ctx* ctx, const void* v0, void* m1_out);
 
+/* Vector-Jacobian product of the map v0 -> m(1) (shoot and transport,
+ * Eqs. 51-52) for any scalar loss of m(1).  grad_m1 [N..] is dLoss/dm(1)
+ * with respect to the grid values; grad_v0_out [d][K..] receives the l2
+ * gradient L~ W(0) with respect to the band coefficients, W the backward
+ * reduced adjoint Jacobi sweep (Eqs. 53-54) started from
+ * U(1) = K~ pi(lambda(1) grad m(1)) with lambda(1) = -N1 N2 N3 grad_m1 (the
+ * L2_h adjoint of the grid values; for the data term of Eq. 50 this is
+ * -(2/sigma^2)(m(1) - I1), so L~^-1 of the result is the data part of
+ * lddmm_gradient).  Runs the forward shoot and transport at v0 first and
+ * leaves it as the linearisation point. */
+int lddmm_transport_vjp(lddmm_ctx* ctx, const void* v0, const void* grad_m1, void* grad_v0_out);
+
 /* dm(1) of the last lddmm_hessvec call (incremental state, Eq. 31). */
 int lddmm_last_dm1(lddmm_ctx* ctx, void* dm1_out);
 

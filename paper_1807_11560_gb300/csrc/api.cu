@@ -992,6 +992,30 @@ struct Impl {
     check_flag(hres[7]);
   }
 
+  // l2 gradient of a loss of m(1) with respect to v0 (adjoint Jacobi sweep)
+  void transport_vjp(const void* v0, const void* gm1, void* out) {
+    need_images();
+    load_bl(v0, vsol);
+    cuda(cudaMemcpyAsync(lin.vh, vsol, (size_t)3 * Kvol * sizeof(C), cudaMemcpyDeviceToDevice, st),
+         "copy v0");
+    forward(lin);
+    cuda(cudaMemcpyAsync(dm[0], gm1, (size_t)Nvol * sizeof(T), cudaMemcpyDefault, st), "copy grad m1");
+    // lambda(1) = -N dL/dm(1): the L2_h adjoint of the grid values
+    terminal_field<T>(lin.mh + (long long)Nt * Nvol, dm[0], 0, -(double)Nvol, fterm, N, st);
+    ++launches;
+    project_K(fterm, U);
+    backward(lin);
+    scale_L<T>(gbuf, W, Lhat, 3, Kvol, st);
+    ++launches;
+    check_launch("transport vjp");
+    store_bl(gbuf, out);
+    cuda(cudaMemcpyAsync(hres + 7, dres + 7, sizeof(double), cudaMemcpyDeviceToHost, st), "read flag");
+    sync("transport vjp");
+    check_flag(hres[7]);
+    have_lin = true;
+    have_dm1 = false;
+  }
+
   void last_dm1(void* out) {
     if (!have_dm1) {
       *err = "no Hessian-vector product computed at this linearisation point";
@@ -1166,6 +1190,13 @@ int lddmm_transport(lddmm_ctx* ctx, const void* v0, void* m1) {
   if (!ctx) return LDDMM_EINVAL;
   if (bad_ptr(ctx, v0, "v0") || bad_ptr(ctx, m1, "m1_out")) return LDDMM_EINVAL;
   return lddmm::dispatch(ctx, [&](auto& im) { im.transport_call(v0, m1); });
+}
+
+int lddmm_transport_vjp(lddmm_ctx* ctx, const void* v0, const void* grad_m1, void* grad_v0) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, v0, "v0") || bad_ptr(ctx, grad_m1, "grad_m1") || bad_ptr(ctx, grad_v0, "grad_v0_out"))
+    return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) { im.transport_vjp(v0, grad_m1, grad_v0); });
 }
 
 int lddmm_last_dm1(lddmm_ctx* ctx, void* out) {

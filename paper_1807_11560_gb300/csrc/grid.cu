@@ -203,6 +203,15 @@ __global__ void k_axpby(cplx<T>* out, T a, const cplx<T>* x, T bc, const cplx<T>
   out[i] = v;
 }
 
+template <typename T>
+__global__ void k_scale_L(cplx<T>* out, const cplx<T>* x, const T* __restrict__ L, long long kvol,
+                          long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T l = L[i % kvol];
+  out[i] = cplx<T>{l * x[i].x, l * x[i].y};
+}
+
 // ---- deterministic FP64 reductions ------------------------------------------------
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double sh[kThreads / 32];
@@ -289,6 +298,11 @@ void axpby(cplx<T>* out, double a, const cplx<T>* x, double bcoef, const cplx<T>
 }
 
 template <typename T>
+void scale_L(cplx<T>* out, const cplx<T>* x, const T* Lhat, int ncomp, long long kvol, cudaStream_t st) {
+  k_scale_L<T><<<blocks_for(ncomp * kvol), kThreads, 0, st>>>(out, x, Lhat, kvol, ncomp * kvol);
+}
+
+template <typename T>
 void sum_sq_diff(const T* a, const T* b, long long n, double* partial, double* out, cudaStream_t st) {
   k_sumsq_diff<T><<<kReduceBlocks, kThreads, 0, st>>>(a, b, n, partial);
   k_finalize<<<1, kThreads, 0, st>>>(partial, kReduceBlocks, out);
@@ -311,6 +325,7 @@ void inner_V(const cplx<T>* a, const cplx<T>* b, const T* Lhat, int ncomp, long 
   template void hermitianize<T>(const cplx<T>*, cplx<T>*, int, Band, cudaStream_t);             \
   template void axpby<T>(cplx<T>*, double, const cplx<T>*, double, const cplx<T>*, long long,    \
                          cudaStream_t);                                                          \
+  template void scale_L<T>(cplx<T>*, const cplx<T>*, const T*, int, long long, cudaStream_t);    \
   template void sum_sq_diff<T>(const T*, const T*, long long, double*, double*, cudaStream_t);   \
   template void inner_V<T>(const cplx<T>*, const cplx<T>*, const T*, int, long long, double*,    \
                            double*, cudaStream_t);

@@ -174,6 +174,9 @@ void hermitianize(const cplx<T>* in, cplx<T>* out, int ncomp, Band b, cudaStream
 template <typename T>
 void axpby(cplx<T>* out, double a, const cplx<T>* x, double bcoef, const cplx<T>* y,
            long long n, cudaStream_t st);
+// out = L^ x per band slot (V representative -> l2 gradient).
+template <typename T>
+void scale_L(cplx<T>* out, const cplx<T>* x, const T* Lhat, int ncomp, long long kvol, cudaStream_t st);
 // FP64 reductions written to a device double (deterministic two-pass tree).
 template <typename T>
 void sum_sq_diff(const T* a, const T* b, long long n, double* partial, double* out,

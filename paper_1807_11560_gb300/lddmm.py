@@ -69,6 +69,7 @@ def lib():
         "lddmm_shoot": (I, [P, P, P]),
         "lddmm_transport": (I, [P, P, P]),
         "lddmm_last_dm1": (I, [P, P]),
+        "lddmm_transport_vjp": (I, [P, P, P, P]),
         "lddmm_kernel_count": (ctypes.c_longlong, [P]),
         "lddmm_probe": (I, [P, ctypes.c_char_p]),
         "lddmm_probe_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong),
@@ -244,6 +245,11 @@ class Context:
     def transport(self, v0, m1_out):
         self._check(lib().lddmm_transport(self._h, self._arg(v0, "cplx", self.nband),
                                           self._arg(m1_out, "real", self.nvox)))
+
+    def transport_vjp(self, v0, grad_m1, out):
+        self._check(lib().lddmm_transport_vjp(self._h, self._arg(v0, "cplx", self.nband),
+                                              self._arg(grad_m1, "real", self.nvox),
+                                              self._arg(out, "cplx", self.nband)))
 
     def last_dm1(self, out):
         self._check(lib().lddmm_last_dm1(self._h, self._arg(out, "real", self.nvox)))

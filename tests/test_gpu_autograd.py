@@ -1,0 +1,96 @@
+"""torch.autograd through the shoot-and-transport map (lddmm_transport_vjp): the
+backward is the library's adjoint Jacobi sweep.  Checked against the FP64 oracle's
+adjoint-Jacobi gradient of the same loss, against the library's own gradient for
+the data term, and against central finite differences of the oracle forward."""
+
+import numpy as np
+import pytest
+
+from oracle import bl, objective, sweeps
+from paper_1807_11560_gb300 import Context, inputs
+from paper_1807_11560_gb300.autograd import shoot_transport
+
+from helpers import ALPHA, S, SIGMA, host, quantise, rel_2, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_l2_grad(P, v0, w):
+    """l2 gradient of sum(w * m(1)) in v0: L~ W(0) from U(1) = K~ pi(-N w grad m(1))."""
+    lin = P.gradient(v0)
+    U1 = P.terminal_U(lin.ms[-1], -float(np.prod(P.Ns)) * w)
+    W0 = sweeps.adjoint_jacobi_backward(lin.vs, lin.vstar, U1, ALPHA, S)
+    return P.L * W0, lin
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_autograd_matches_oracle_adjoint_gradient(precision):
+    import torch
+    Ns, Ks, Nt = (20, 18, 16), (8, 6, 6), 4
+    I0, I1 = inputs.make_pair("ellipsoids", Ns, 31, max_disp=2.0)
+    I0, I1 = quantise(I0, precision), quantise(I1, precision)
+    v0 = quantise(inputs.random_bl(Ks, 3, 32, 2.0, Ns), precision)
+    w = quantise(np.random.default_rng(33).normal(size=Ns), precision)
+    ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision=precision)
+    ctx.set_images(torch_dev(I0, precision), torch_dev(I1, precision))
+    v = torch_dev(v0, precision).requires_grad_(True)
+    m1 = shoot_transport(ctx, v)
+    (m1 * torch_dev(w, precision)).sum().backward()
+    P = objective.Problem(I0, I1, Ks, ALPHA, S, SIGMA, Nt)
+    g_ref, lin = _oracle_l2_grad(P, v0, w)
+    tol = 1e-9 if precision == "fp64" else 1e-5
+    assert rel_2(host(m1.detach()), lin.ms[-1]) < tol
+    assert rel_2(host(v.grad), g_ref) < tol
+
+
+def test_autograd_of_the_data_term_is_the_library_gradient():
+    import torch
+    Ns, Ks, Nt = (20, 18, 16), (8, 6, 6), 4
+    I0, I1 = inputs.make_pair("ellipsoids", Ns, 34, max_disp=2.0)
+    v0 = inputs.random_bl(Ks, 3, 35, 2.0, Ns)
+    ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision="fp64")
+    ctx.set_images(torch_dev(I0, "fp64"), torch_dev(I1, "fp64"))
+    v = torch_dev(v0, "fp64").requires_grad_(True)
+    m1 = shoot_transport(ctx, v)
+    I1d = torch_dev(I1, "fp64")
+    loss = ((m1 - I1d) ** 2).mean() / SIGMA ** 2            # h^d sum = mean on the unit box
+    loss.backward()
+    g = torch.empty_like(v)
+    ctx.gradient(torch_dev(v0, "fp64"), g)
+    L = bl.lhat(Ks, ALPHA, S)
+    data_part = host(g) - v0                                  # V-gradient minus the regulariser
+    np.testing.assert_allclose(host(v.grad) / L, data_part, atol=1e-10 * np.abs(data_part).max())
+
+
+def test_differentiation_check_96cubed():
+    """The 96^3 brain configuration, band 24^3, Nt = 16: GPU FP32 autograd against the
+    FP64 oracle's adjoint gradient (1e-5) and central differences of the FP64 oracle
+    forward (step 1e-3; the gap is the discretisation gap of the paper-form gradient)."""
+    import torch
+    kind, Ns, Ks, Nt, seed = inputs.WORKLOADS["3d_96_brain"]
+    I0, I1 = inputs.make_pair(kind, Ns, seed)
+    I0, I1 = quantise(I0, "fp32"), quantise(I1, "fp32")
+    v0 = quantise(inputs.random_bl(Ks, 3, seed + 1, 2.0, Ns), "fp32")
+    free0 = torch.cuda.mem_get_info()[0]
+    ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision="fp32")
+    footprint = free0 - torch.cuda.mem_get_info()[0]
+    ctx.set_images(torch_dev(I0, "fp32"), torch_dev(I1, "fp32"))
+    v = torch_dev(v0, "fp32").requires_grad_(True)
+    m1 = shoot_transport(ctx, v)
+    I1d = torch_dev(I1, "fp32")
+    (((m1 - I1d) ** 2).mean() / SIGMA ** 2).backward()
+    g = host(v.grad)
+    P = objective.Problem(I0, I1, Ks, ALPHA, S, SIGMA, Nt)
+    lin = P.gradient(v0)
+    g_ref = P.L * (lin.g - v0)                               # l2 form of the data part
+    assert rel_2(g, g_ref) < 1e-5
+    gaps = []
+    for s in range(2000, 2003):
+        p = inputs.random_bl(Ks, 3, s, 1.0, Ns)
+        eps = 1e-3
+        Ep = P.data_term(P.forward(v0 + eps * p)[3][-1])
+        Em = P.data_term(P.forward(v0 - eps * p)[3][-1])
+        fd = (Ep - Em) / (2 * eps)
+        gaps.append(abs(fd - bl.inner_l2(g, p)) / abs(fd))
+    print(f"96^3: context footprint {footprint / 2**20:.0f} MiB; FD gaps {gaps}")
+    assert max(gaps) < 0.2

@@ -52,3 +52,11 @@ def test_brain_workload_160x192x160():
     assert rel_V(g, gr, Ks) < 1e-5
     assert rel_V(Hp, Hr, Ks) < 1e-5
     assert rel_2(m1, mr) < 1e-5
+
+
+def test_differentiation_workload_96cubed_nt16():
+    (E, g, Hp, m1), (Er, gr, Hr, mr), Ks = _run("3d_96_brain", 2.0)
+    assert abs(E - Er) / Er < 1e-6
+    assert rel_V(g, gr, Ks) < 1e-5
+    assert rel_V(Hp, Hr, Ks) < 1e-5
+    assert rel_2(m1, mr) < 1e-5
