@@ -227,6 +227,24 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
     fh += kThreads / TP;
     if (pp >= TP) { pp -= TP; ++fh; }
   }
+  // the cached stage-point fields of this thread's (up to 2) product points,
+  // fetched now so their latency overlaps the transform stage
+  const long long fs = (long long)G1 * P;                  // field stride of a slot
+  T cv[2][12], cl[2][12];
+  if (MODE != PW_F) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int i = tid + r * kThreads;
+      const int x1 = i / TP, pp = i - (i / TP) * TP;
+      const bool ok = i < G1 * TP && p0 + pp < P;
+      const T* __restrict__ cs = slot + (long long)x1 * P + p0 + pp;
+#pragma unroll
+      for (int f = 0; f < 12; ++f) {
+        cv[r][f] = ok ? cs[f * fs] : T(0);
+        cl[r][f] = ok ? cs[(12 + f) * fs] : T(0);
+      }
+    }
+  }
   for (int i = tid; i < H1 * G1q; i += kThreads) {
     const int h = i / G1q, x = i - h * G1q;
     sE1f[i] = x < G1 ? p.E1f[h * G1 + x] : zero;
@@ -236,7 +254,6 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
     sE1b[i] = h < H1 ? p.E1b[x * H1 + h] : zero;
   }
   __syncthreads();
-  const long long fs = (long long)G1 * P;                  // field stride of a slot
   const int nq = G1q / 4;
   for (int it = tid; it < 24 * TP * nq; it += kThreads) {  // C: 24 grid fields, 4 planes each
     const int f = it / (TP * nq);                          // pencil fastest: the sT2 reads are
@@ -266,7 +283,10 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
     }
   }
   __syncthreads();
-  for (int i = tid; i < G1 * TP; i += kThreads) {          // bracket products
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {                           // bracket products
+    const int i = tid + r * kThreads;
+    if (i >= G1 * TP) break;
     const int x1 = i / TP, pp = i - x1 * TP;
     T o[9];
 #pragma unroll
@@ -280,22 +300,13 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
       }
       if (MODE == PW_F) {
         bracketP(xv, xl, o);                               // P(v, L v)
+      } else if (MODE == PW_T) {
+        bracketP(xv, cl[r], o);                            // P(dv, L v)
+        bracketP(cv[r], xl, o);                            // P(v, L dv)
       } else {
-        T cv[12], cl[12];
-        const T* __restrict__ cs = slot + (long long)x1 * P + p0 + pp;
-#pragma unroll
-        for (int f = 0; f < 12; ++f) {
-          cv[f] = cs[f * fs];
-          cl[f] = cs[(12 + f) * fs];
-        }
-        if (MODE == PW_T) {
-          bracketP(xv, cl, o);                             // P(dv, L v)
-          bracketP(cv, xl, o);                             // P(v, L dv)
-        } else {
-          bracketP(cv, xl, o);                             // P(v, L U)
-          bracketP(xv, cl, o + 3);                         // P(W, L v)
-          bracketQ(cv, xv, o + 6);                         // Q(v, W)
-        }
+        bracketP(cv[r], xl, o);                            // P(v, L U)
+        bracketP(xv, cl[r], o + 3);                        // P(W, L v)
+        bracketQ(cv[r], xv, o + 6);                        // Q(v, W)
       }
     }
 #pragma unroll
@@ -412,20 +423,19 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
   }
   __syncthreads();
 
-  // A' + epilogue: kRed consecutive lanes share one band slot (c, h, kb+kk, k3)
+  // A': kRed consecutive lanes share one band-slot sum; the sums of every
+  // product field go to shared memory (Y [nslot][nper], over the slab area)
   const int nslot = kc * K3;
+  C* Y = slab;                                             // slab no longer read (synced above)
   for (int base = 0; base < nslot * kRed; base += kThreads) {
     const int lin = base + tid;
     const int it = lin / kRed, part = lin % kRed;
     const bool live = it < nslot;
     const int kk = live ? it / K3 : 0;
     const int k3 = live ? it - kk * K3 : 0;
-    const int k2 = kb + kk;
-    const bool nq = !live || nyq(k2, K2) || nyq(k3, K3);
-    C R[2] = {zero, zero};
     for (int o = 0; o < nper; ++o) {
       C y = zero;
-      if (!nq) {
+      if (live) {
         const C* row = S1 + (o * KC + kk) * G3;
         const C* er = E3s + k3 * G3;
         for (int x = part; x < G3; x += kRed) cmac(y, row[x], er[x]);
@@ -435,26 +445,39 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
         y.x += __shfl_down_sync(0xffffffffu, y.x, off, kRed);
         y.y += __shfl_down_sync(0xffffffffu, y.y, off, kRed);
       }
-      if (part == 0 && !nq) {
-        const long long kin = ((long long)h * K2 + k2) * K3 + k3;
-        const T sc = e.coef[o] * (e.applyK[o] ? T(1) / Lhat[kin] : T(1));
+      if (part == 0 && live) Y[it * nper + o] = y;
+    }
+  }
+  __syncthreads();
+  // epilogue: one band slot per thread, every global load of a slot issued at once
+  for (int it = tid; it < nslot; it += kThreads) {
+    const int kk = it / K3, k3 = it - kk * K3;
+    const int k2 = kb + kk;
+    const bool nq = nyq(k2, K2) || nyq(k3, K3);
+    const long long kin = ((long long)h * K2 + k2) * K3 + k3;
+    const long long at = (long long)c * kvol + kin;
+    // read every X term before any write: outputs may alias inputs
+    C xs[kMaxOut][kMaxX];
+    for (int j = 0; j < nout; ++j)
+      for (int q = 0; q < e.nx[j]; ++q) xs[j][q] = e.X[j][q][at];
+    const T kh = T(1) / Lhat[kin];
+    C R[2] = {zero, zero};
+    if (!nq) {
+      for (int o = 0; o < nper; ++o) {
+        const C y = Y[it * nper + o];
+        const T sc = e.coef[o] * (e.applyK[o] ? kh : T(1));
         R[e.grp[o]].x += sc * y.x;
         R[e.grp[o]].y += sc * y.y;
       }
     }
-    if (part != 0 || !live) continue;
-    const long long kin = ((long long)h * K2 + k2) * K3 + k3;
-    const long long at = (long long)c * kvol + kin;
-    // read every X term before any write: outputs may alias inputs
     C val[kMaxOut];
     for (int j = 0; j < nout; ++j) {
       C v = zero;
       if (!nq) {
         if (e.r[j] >= 0) { v.x = e.cR[j] * R[e.r[j]].x; v.y = e.cR[j] * R[e.r[j]].y; }
         for (int q = 0; q < e.nx[j]; ++q) {
-          const C xv = e.X[j][q][at];
-          v.x += e.cX[j][q] * xv.x;
-          v.y += e.cX[j][q] * xv.y;
+          v.x += e.cX[j][q] * xs[j][q].x;
+          v.y += e.cX[j][q] * xs[j][q].y;
         }
       }
       val[j] = v;
@@ -496,7 +519,8 @@ template <typename T>
 inline int cpw_tile(const Plan<T>& p) {
   const long long P = (long long)p.g.n2 * p.g.n3;
   int TP = (int)std::max(1LL, std::min(8LL, P / 152));
-  while (TP > 1 && cpw_smem(p, TP, 9) > (size_t)kMaxSmem) --TP;
+  // products: at most two points per thread, and the tile must fit shared memory
+  while (TP > 1 && (cpw_smem(p, TP, 9) > (size_t)kMaxSmem || p.g.n1 * TP > 2 * kThreads)) --TP;
   return TP;
 }
 
@@ -512,7 +536,8 @@ inline BAGeom ba_geom(const Plan<T>& p, int ncomp, int nper) {
   const size_t fixed = ((size_t)G2 * KC + (size_t)G3 * K3 + (size_t)nper * KC * G3) * c;
   const size_t budget = fixed < (size_t)kMaxSmem ? (size_t)kMaxSmem - fixed : 0;
   const size_t rows = std::min<size_t>(budget, 96 * 1024) / ((size_t)nper * G3 * c);
-  const int XB = (int)std::min<size_t>((size_t)G2, std::max<size_t>(1, rows));
+  // the slab area later holds the A' sums of kc * K3 slots: XB >= KC suffices (G3 >= K3)
+  const int XB = std::max(KC, (int)std::min<size_t>((size_t)G2, std::max<size_t>(1, rows)));
   return BAGeom{KC, nch, XB};
 }
 

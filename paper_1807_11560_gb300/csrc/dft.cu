@@ -169,6 +169,7 @@ size_t max_smem_needed(const Plan<T>& p, int nper_max, bool brackets) {
   if (p.b.h1 > kMaxH1Reg) return ~size_t(0);
   if ((size_t)p.b.h1 * p.g.n1 * sizeof(cplx<T>) > (size_t)kMaxSmem) return ~size_t(0);
   const size_t ab = dev::ab_smem(p, dev::ab_tws(p));
+  if (brackets && p.g.n1 > 2 * kThreads) return ~size_t(0);
   const size_t cpw = brackets ? dev::cpw_smem(p, dev::cpw_tile(p), 9) : 0;
   size_t ba = 0;
   for (int nper = 1; nper <= nper_max; ++nper)
