@@ -186,6 +186,31 @@ def combine_ranks(t_sec, n_hv, world, device):
 
 
 # --------------------------------------------------------------------------- GPU arm
+def kernel_sources_hash():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1807_11560_gb300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload_name, cls):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary, or
+    None when there is none or the CUDA sources changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        data = json.load(f)
+    if data.get("kernel_sources_sha256_16") != kernel_sources_hash():
+        return None
+    entry = data.get(workload_name, {}).get(cls)
+    return None if entry is None else float(entry["bytes"])
+
+
 PROBE_CLASSES = ("sweep", "iota_ab", "cpw", "pi_ba", "inc_step", "transport", "iota_full", "pi_full")
 HBM_CLASSES = ("inc_step", "transport")
 SMS, FP32_LANES = 152, 128
@@ -335,7 +360,8 @@ def run_gpu(args):
                                    "(median sampled SM clock); FP32 SIMT contraction"}
             wunit = "flop"
         roof.update({"kernel": probe_cls, "achieved": achieved, "peak": peak, "frac": achieved / peak,
-                     "traffic": None, "launches_timed": probe_n, "avg_launch_us": avg_s * 1e6,
+                     "traffic": measured_traffic(name, probe_cls), "traffic_unit": "B per launch (ncu)",
+                     "launches_timed": probe_n, "avg_launch_us": avg_s * 1e6,
                      "algorithmic_per_launch": work, "algorithmic_unit": wunit,
                      "measured": f"CUDA events around each launch over a second pass of the {args.steps} "
                                  "timed steps"})
