@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--workload", default="3d_64_ellipsoids")
     ap.add_argument("--probe", default="auto", help="kernel class timed for the roofline (auto: dominant)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tensor-cores", default="auto", choices=["auto", "on", "off"],
+                    help="image-grid band-to-grid transforms on tcgen05 (3xTF32): auto = grids >= 2^20 voxels")
     return ap.parse_args()
 
 
@@ -249,7 +251,8 @@ def run_gpu(args):
     I0, I1 = inputs.make_pair(kind, Ns, rank_seed(seed, rank))
     I0d = torch.as_tensor(I0, dtype=torch.float32, device=dev)
     I1d = torch.as_tensor(I1, dtype=torch.float32, device=dev)
-    ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision="fp32")
+    ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision="fp32",
+                  tensor_cores={"auto": "auto", "on": True, "off": False}[args.tensor_cores])
     ctx.set_images(I0d, I1d)
     v = torch.zeros((d,) + tuple(Ks), dtype=torch.complex64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -382,7 +385,9 @@ def run_gpu(args):
             "config": {"workload": name, "grid": list(Ns), "band": list(Ks), "Nt": Nt,
                        "pcg_per_gn": N_PCG, "step": "one GN iteration (gradient, 20 PCG Hessvecs, Armijo)",
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "tensor_cores": f"{args.tensor_cores} (tcgen05 3xTF32 image-grid iota; "
+                                       "auto = grids of at least 2^20 voxels)"},
             "gn_solve_s": 1e-3 * statistics.mean(step_ms) * N_GN_CONFIG,
             "gn_solve_note": f"{N_GN_CONFIG} GN x {N_PCG} PCG at the mean timed step time",
             "hessvec_per_s_fixed_point": hv_fixed,

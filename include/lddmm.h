@@ -87,6 +87,9 @@ typedef struct {
                            (grid barriers with bounded waits): 0 never (three kernels per
                            bracket evaluation), 1 when the padded product grid has at
                            most 32^3 points (default), 2 always */
+  int tensor_cores;     /* FP32 contexts: band-to-image-grid transforms (iota stage C) on
+                           the tcgen05 tensor cores with the 3xTF32 split: 0 never,
+                           1 for image grids of at least 2^20 voxels (default), 2 always */
 } lddmm_opts;
 
 /* Report of lddmm_gn_solve.  The per-iteration arrays are optional
@@ -105,7 +108,8 @@ typedef struct {
 } lddmm_report;
 
 /* Defaults for lddmm_opts (precision FP32, legacy stream, tol 1e-12,
- * c = 1e-4, 10 halvings, graphs on, persistent sweeps on small grids). */
+ * c = 1e-4, 10 halvings, graphs on, persistent sweeps on small grids,
+ * tensor-core image-grid transforms on large grids). */
 void lddmm_default_opts(lddmm_opts* opts);
 
 /* Create a registration context (Section 3.2).

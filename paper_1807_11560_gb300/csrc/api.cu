@@ -293,7 +293,7 @@ struct Impl {
   // a persistent sweep whose barrier wait gave up left dres[7] = 1
   void check_flag(double f) {
     if (f != 0.0) {
-      *err = "a persistent sweep barrier wait timed out";
+      *err = "a bounded device wait (sweep barrier or tensor-core MMA) timed out";
       throw Fail{LDDMM_ETIMEOUT};
     }
   }
@@ -460,6 +460,11 @@ struct Impl {
   // persistent sweeps pay off while the phases are latency-bound (small padded
   // grids); beyond that one launch's worst-phase footprint costs occupancy
   static constexpr long long kPersistentMaxPadded = 32768;   // M1 M2 M3
+  // tensor-core image-grid transforms pay off once the grid write dominates
+  static constexpr long long kTensorMinVoxels = 1LL << 20;
+  bool use_tc() const {
+    return opts.tensor_cores == 2 || (opts.tensor_cores == 1 && Nvol >= kTensorMinVoxels);
+  }
   bool persistent() const {
     if (rec != nullptr || opts.persistent == 0) return false;
     return opts.persistent == 2 || Mvol <= kPersistentMaxPadded;
@@ -487,7 +492,7 @@ struct Impl {
           d.applyL[f] = 0;
         }
       pb(PR_IOTA_FULL);
-      iota_batch<T>(full, d, Lhat, T2, st);
+      iota_batch<T>(full, d, Lhat, T2, st, use_tc() ? dres + 7 : nullptr);
       pe(PR_IOTA_FULL, iota_flops(d.nf));
       launches += kIotaLaunches;
     }
@@ -913,13 +918,15 @@ struct Impl {
         d.deriv[c] = -1;
         d.applyL[c] = 0;
       }
-      iota_batch<T>(full, d, Lhat, T2, st);
+      iota_batch<T>(full, d, Lhat, T2, st, use_tc() ? dres + 7 : nullptr);
       launches += kIotaLaunches;
       check_launch("iota");
       cuda(cudaMemcpyAsync((T*)out + (long long)c0 * Nvol, fterm, (size_t)nc * Nvol * sizeof(T),
                            cudaMemcpyDefault, st), "copy");
     }
+    cuda(cudaMemcpyAsync(hres + 7, dres + 7, sizeof(double), cudaMemcpyDeviceToHost, st), "read flag");
     sync("iota");
+    check_flag(hres[7]);
   }
 
   void pi_call(const void* f, int ncomp, void* out) {
@@ -1074,6 +1081,7 @@ void lddmm_default_opts(lddmm_opts* o) {
   o->max_halvings = 10;
   o->use_graphs = 1;
   o->persistent = 1;
+  o->tensor_cores = 1;
 }
 
 int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, double alpha, int s,

@@ -503,9 +503,11 @@ __host__ __device__ inline size_t ab_smem(const Plan<T>& p, bool tws) {
   return n * sizeof(cplx<T>);
 }
 
+// stage the twiddles only while the tile stays small enough for several CTAs
+// per SM (large image-grid planes are latency-bound at one CTA per SM)
 template <typename T>
 __host__ __device__ inline bool ab_tws(const Plan<T>& p) {
-  return ab_smem(p, true) <= (size_t)kMaxSmem;
+  return ab_smem(p, true) <= (size_t)64 * 1024;
 }
 
 template <typename T>

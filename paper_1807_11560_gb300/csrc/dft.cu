@@ -193,8 +193,21 @@ void launch_Cb(const Plan<T>& p, const PiSrc<T>& s, cplx<T>* P2, unsigned grid, 
 }
 
 template <typename T>
-void iota_batch(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2, cudaStream_t st) {
+bool try_tc(const Plan<T>&, const IotaDesc<T>&, const cplx<T>*, double*, cudaStream_t) {
+  return false;
+}
+template <>
+bool try_tc<float>(const Plan<float>& p, const IotaDesc<float>& d, const float2* T2, double* flag,
+                   cudaStream_t st) {
+  if (!flag || !iota_C_tc_supported(p)) return false;
+  return iota_C_tc(p, d, T2, flag, st) == cudaSuccess;
+}
+
+template <typename T>
+void iota_batch(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2, cudaStream_t st,
+                double* tc_flag) {
   launch_iota_AB<T>(p, d, Lhat, T2, st);
+  if (try_tc<T>(p, d, T2, tc_flag, st)) return;
   const long long nblk = ((long long)p.g.n2 * p.g.n3 + kThreads - 1) / kThreads;
   const size_t smem = (size_t)p.b.h1 * p.g.n1 * sizeof(cplx<T>);
   const unsigned grid = (unsigned)(d.nf * nblk);
@@ -250,7 +263,8 @@ void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T
 
 #define LDDMM_DFT_INST(T)                                                                          \
   template size_t max_smem_needed<T>(const Plan<T>&, int, bool);                                   \
-  template void iota_batch<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t); \
+  template void iota_batch<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t,    \
+                              double*);                                                            \
   template void pi_batch<T>(const Plan<T>&, const PiSrc<T>&, const PiEpi<T>&, const T*, cplx<T>*,  \
                             cudaStream_t);                                                         \
   template void bracket_iota<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t); \

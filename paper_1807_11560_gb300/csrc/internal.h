@@ -94,9 +94,15 @@ struct PiEpi {
 // ---- transforms (dft.cu) --------------------------------------------------
 // Scratch: T2 holds [F][h1][G2][G3] complex (iota intermediate, and the C'
 // output of pi), P2 holds [9][h1][M2][M3] complex (C' of a bracket evaluation).
+// tc_flag != nullptr selects the tcgen05 3xTF32 form of stage C (FP32 plans
+// it supports); the kernel sets *tc_flag = 1 if its bounded MMA wait gives up.
 template <typename T>
 void iota_batch(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2,
-                cudaStream_t st);
+                cudaStream_t st, double* tc_flag = nullptr);
+// tcgen05 image-grid stage C (tc_iota.cu)
+bool iota_C_tc_supported(const Plan<float>& p);
+cudaError_t iota_C_tc(const Plan<float>& p, const IotaDesc<float>& d, const float2* T2, double* flag,
+                      cudaStream_t st);
 template <typename T>
 void pi_batch(const Plan<T>& p, const PiSrc<T>& s, const PiEpi<T>& e, const T* Lhat,
               cplx<T>* P2, cudaStream_t st);

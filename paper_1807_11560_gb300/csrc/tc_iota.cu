@@ -1,0 +1,266 @@
+// Tensor-core (tcgen05, sm_103a) form of the image-grid iota stage C, the
+// k1 -> x1 contraction of the band-limited-to-grid map (Eq. 46):
+//
+//   out_f[x1][i] = sum_h Re(E1f[h][x1] T2[f][h][i]) = sum_k A[x1][k] B_f[k][i]
+//   A[x1][2h] = Re E1f[h][x1],  A[x1][2h+1] = -Im E1f[h][x1]
+//   B_f[2h][i] = Re T2[f][h][i], B_f[2h+1][i] = Im T2[f][h][i]
+//
+// a real GEMM with M = N1 (x1), K = K1 (padded to a multiple of 8) and
+// N = N2 N3 per field.  FP32 accuracy from TF32 tensor cores by the 3xTF32
+// split x = hi + lo (hi = TF32 rounding of x): A B ~ Ahi Bhi + Ahi Blo + Alo Bhi,
+// accumulated in FP32 in tensor memory.
+//
+// One CTA (256 threads) owns up to two 128-row M tiles (N1 <= 256) in 256
+// TMEM columns and walks (field, 128-column N tile) work items:
+//   1. all threads stage B (hi and lo) into shared memory in the K-major,
+//      no-swizzle canonical layout (8 x 16-byte core matrices);
+//   2. one thread issues the MMAs and commits them to an mbarrier;
+//   3. all threads wait (bounded), read their TMEM lane quadrant with
+//      tcgen05.ld and store rows of out.
+// A (the twiddles) is staged once per CTA.  D leaves TMEM in 32-column chunks
+// through a padded shared tile so that every warp stores 128 contiguous bytes.
+// At least 96 KB of shared memory keeps at most two CTAs on an SM, so the two
+// 256-column TMEM allocations always fit.
+#include <algorithm>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace lddmm {
+namespace {
+
+constexpr int kThreadsTC = 256;
+constexpr int kNT = 128;                 // N tile (columns of D per M tile)
+constexpr int kMT = 128;                 // M tile (TMEM lanes)
+constexpr int kMaxKp = 48;               // K1 <= 48 (shared memory)
+constexpr long long kWaitLimit = 1LL << 24;
+constexpr int kStile = 128 * 33 + 4;     // padded D chunk, rounded to 16 bytes
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// float offset of element (row r, k) in a K-major no-swizzle operand tile with
+// Kp columns: core matrix (r/8, k/4) of 8 rows x 4 elements, rows 16 bytes apart
+__device__ __forceinline__ int kmajor_off(int r, int k, int Kp) {
+  return (((r >> 3) * (Kp >> 2) + (k >> 2)) << 5) + ((r & 7) << 2) + (k & 3);
+}
+
+// tcgen05 shared-memory descriptor: no swizzle, K-major; LBO = distance of
+// K-adjacent core matrices, SBO = distance of 8-row groups (bytes).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__global__ void __launch_bounds__(kThreadsTC)
+k_iota_C_tc(Plan<float> p, IotaDesc<float> d, const float2* __restrict__ T2, int Kp, int nmt, double* flag) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  float* sm = reinterpret_cast<float*>(smraw);
+  const int tileA = kMT * Kp, tileB = kNT * Kp;
+  float* Ahi[2] = {sm, sm + 2 * tileA};
+  float* Alo[2] = {sm + tileA, sm + 3 * tileA};
+  float* Bhi = sm + 4 * tileA;
+  float* Blo = Bhi + tileB;
+  float* stile = Blo + tileB;                                // [128][33] D chunk for coalesced stores
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(stile + kStile);   // 16-byte aligned
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+  const int G1 = p.g.n1, H1 = p.b.h1, K = 2 * H1;
+  const long long P = (long long)p.g.n2 * p.g.n3;
+  const int ntn = (int)((P + kNT - 1) / kNT);
+  const long long nitems = (long long)d.nf * ntn;
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  // A (both M tiles) and the zero K padding of B, once per CTA
+  for (int idx = tid; idx < 2 * kMT * Kp; idx += kThreadsTC) {
+    const int mt = idx / (kMT * Kp), rem = idx - mt * kMT * Kp;
+    const int r = rem / Kp, k = rem - r * Kp;
+    const int x1 = mt * kMT + r;
+    float v = 0.f;
+    if (x1 < G1 && k < K) {
+      const float2 e = p.E1f[(k >> 1) * G1 + x1];
+      v = (k & 1) ? -e.y : e.x;
+    }
+    const float hi = tf32_hi(v);
+    const int o = kmajor_off(r, k, Kp);
+    Ahi[mt][o] = hi;
+    Alo[mt][o] = v - hi;
+  }
+  for (int idx = tid; idx < kNT * (Kp - K); idx += kThreadsTC) {
+    const int r = idx / (Kp - K), k = K + idx % (Kp - K);
+    Bhi[kmajor_off(r, k, Kp)] = 0.f;
+    Blo[kmajor_off(r, k, Kp)] = 0.f;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tslot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = *tslot;
+
+  const uint32_t idesc = idesc_tf32(kMT, kNT);
+  const uint32_t lbo = 128, sbo = (uint32_t)(Kp >> 2) * 128;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+    const int f = (int)(item / ntn);
+    const long long n0 = (item % ntn) * kNT;
+    // 1. B tile, hi and lo
+    const float2* __restrict__ src = T2 + (long long)f * H1 * P + n0;
+    for (int idx = tid; idx < H1 * kNT; idx += kThreadsTC) {
+      const int h = idx / kNT, r = idx - h * kNT;
+      const float2 t = (n0 + r < P) ? src[(long long)h * P + r] : make_float2(0.f, 0.f);
+      const float hr = tf32_hi(t.x), hi_ = tf32_hi(t.y);
+      const int o = kmajor_off(r, 2 * h, Kp);
+      *reinterpret_cast<float2*>(Bhi + o) = make_float2(hr, hi_);
+      *reinterpret_cast<float2*>(Blo + o) = make_float2(t.x - hr, t.y - hi_);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    // 2. MMAs, one issuing thread
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int mt = 0; mt < nmt; ++mt) {
+        const uint32_t dcol = tbase + (uint32_t)(mt * kNT);
+        for (int s = 0; s < Kp / 8; ++s) {
+          const uint32_t so = (uint32_t)s * 256;
+          const uint64_t ah = smem_desc(smem_u32(Ahi[mt]) + so, lbo, sbo);
+          const uint64_t al = smem_desc(smem_u32(Alo[mt]) + so, lbo, sbo);
+          const uint64_t bh = smem_desc(smem_u32(Bhi) + so, lbo, sbo);
+          const uint64_t bl = smem_desc(smem_u32(Blo) + so, lbo, sbo);
+          mma_tf32(dcol, ah, bh, idesc, s > 0 ? 1u : 0u);
+          mma_tf32(dcol, ah, bl, idesc, 1u);
+          mma_tf32(dcol, al, bh, idesc, 1u);
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(mbar))
+                   : "memory");
+    }
+    // 3. wait for the MMAs (bounded), then read D and store
+    long long it = 0;
+    while (!mbar_try_wait(smem_u32(mbar), phase)) {
+      if (++it > kWaitLimit) {
+        ok = false;
+        break;
+      }
+    }
+    phase ^= 1u;
+    if (!__syncthreads_and(ok ? 1 : 0)) {
+      ok = false;
+      if (tid == 0) *(volatile double*)flag = 1.0;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // each warp reads 16 columns of its 32-lane quadrant into a padded shared
+    // tile; then every warp stores 32 consecutive floats of one row of out
+    const int q = warp & 3, half = warp >> 2;
+    const int r = 32 * q + (tid & 31);
+    for (int mt = 0; mt < nmt; ++mt) {
+      for (int c0 = 0; c0 < kNT; c0 += 32) {
+        float v[16];
+        tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * kNT + c0 + 16 * half), v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) stile[r * 33 + 16 * half + j] = v[j];
+        __syncthreads();
+        for (int e = tid; e < kMT * 32; e += kThreadsTC) {
+          const int row = e >> 5, col = e & 31;
+          const int x1 = mt * kMT + row;
+          const long long n = n0 + c0 + col;
+          if (x1 < G1 && n < P) d.dst[f][(long long)x1 * P + n] = stile[row * 33 + col];
+        }
+        __syncthreads();
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tbase) : "memory");
+}
+
+}  // namespace
+
+size_t iota_C_tc_smem(int K1) {
+  const int Kp = ((K1 + 7) / 8) * 8;
+  return (size_t)(4 * kMT * Kp + 2 * kNT * Kp + kStile) * sizeof(float) + 16;
+}
+
+bool iota_C_tc_supported(const Plan<float>& p) {
+  const int Kp = ((2 * p.b.h1 + 7) / 8) * 8;
+  return p.g.n1 <= 2 * kMT && Kp <= kMaxKp && iota_C_tc_smem(2 * p.b.h1) <= 200 * 1024;
+}
+
+cudaError_t iota_C_tc(const Plan<float>& p, const IotaDesc<float>& d, const float2* T2, double* flag,
+                      cudaStream_t st) {
+  const int Kp = ((2 * p.b.h1 + 7) / 8) * 8;
+  const int nmt = (p.g.n1 + kMT - 1) / kMT;
+  // at least 96 KB per CTA: at most two CTAs (two 256-column TMEM allocations) per SM
+  const size_t smem = std::max<size_t>(iota_C_tc_smem(2 * p.b.h1), 96 * 1024 + 16);
+  cudaError_t e = cudaFuncSetAttribute(k_iota_C_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const long long P = (long long)p.g.n2 * p.g.n3;
+  const long long items = (long long)d.nf * ((P + kNT - 1) / kNT);
+  const unsigned grid = (unsigned)std::min<long long>(items, 2LL * sms);
+  k_iota_C_tc<<<grid, kThreadsTC, smem, st>>>(p, d, T2, Kp, nmt, flag);
+  return cudaGetLastError();
+}
+
+}  // namespace lddmm

@@ -31,7 +31,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("pcg_tol", ctypes.c_double), ("armijo_c", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("persistent", ctypes.c_int)]
+                ("persistent", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -122,7 +122,8 @@ class Context:
     """
 
     def __init__(self, grid, K, alpha, s, sigma, Nt, precision="fp32", stream=None,
-                 use_graphs=True, pcg_tol=1e-12, armijo_c=1e-4, max_halvings=10, persistent="auto"):
+                 use_graphs=True, pcg_tol=1e-12, armijo_c=1e-4, max_halvings=10, persistent="auto",
+                 tensor_cores="auto"):
         L = lib()
         self.grid, self.K = tuple(int(g) for g in grid), tuple(int(k) for k in K)
         self.ndim = len(self.grid)
@@ -135,6 +136,7 @@ class Context:
         o.stream = stream
         o.use_graphs = 1 if use_graphs else 0
         o.persistent = {True: 2, False: 0, "auto": 1}[persistent]
+        o.tensor_cores = {True: 2, False: 0, "auto": 1}[tensor_cores]
         o.pcg_tol, o.armijo_c, o.max_halvings = pcg_tol, armijo_c, max_halvings
         arr = ctypes.c_int * self.ndim
         h = ctypes.c_void_p()

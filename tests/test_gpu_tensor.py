@@ -1,0 +1,47 @@
+"""The tcgen05 (3xTF32) form of the image-grid band-to-grid transform against the
+FP64 oracle, and end to end inside the gradient and Hessian-vector product."""
+
+import numpy as np
+import pytest
+
+from oracle import bl
+from paper_1807_11560_gb300 import Context, inputs
+
+from helpers import ALPHA, S, SIGMA, host, problem, quantise, rel_2, rel_V, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+# (grid, band): K1 padding (10 -> 16), one and two 128-row M tiles, ragged N tiles
+SHAPES = [((64, 64, 64), (16, 16, 16)), ((100, 36, 20), (10, 8, 6)), ((200, 24, 26), (24, 8, 8)),
+          ((160, 192, 160), (32, 32, 32)), ((48, 40), (16, 12))]
+
+
+@pytest.mark.parametrize("Ns,Ks", SHAPES)
+def test_tensor_core_iota_matches_oracle(Ns, Ks):
+    import torch
+    d = len(Ns)
+    a = quantise(inputs.random_bl(Ks, d, 3, 2.0, Ns), "fp32")
+    ref = bl.iota(a, Ns)
+    outs = []
+    for tc in (True, False):
+        ctx = Context(Ns, Ks, ALPHA, S, SIGMA, 2, precision="fp32", tensor_cores=tc)
+        out = torch.empty((d,) + Ns, device="cuda", dtype=torch.float32)
+        ctx.iota(torch_dev(a, "fp32"), d, out)
+        outs.append(host(out))
+        ctx.close()
+    err_tc, err_simt = rel_2(outs[0], ref), rel_2(outs[1], ref)
+    assert err_tc < 4e-6, (err_tc, err_simt)
+
+
+def test_tensor_core_gradient_and_hessvec():
+    kind, Ns, Ks, seed, Nt = "ellipsoids", (40, 36, 34), (12, 10, 8), 41, 4
+    ctx, P, v0, p = problem(kind, Ns, Ks, seed, Nt, "fp32", tensor_cores=True)
+    import torch
+    lin = P.gradient(v0)
+    g = torch.empty((3,) + Ks, device="cuda", dtype=torch.complex64)
+    E = ctx.gradient(torch_dev(v0, "fp32"), g)
+    Hp = torch.empty_like(g)
+    ctx.hessvec(torch_dev(p, "fp32"), Hp)
+    assert abs(E - lin.E) / lin.E < 1e-6
+    assert rel_V(host(g), lin.g, Ks) < 1e-5
+    assert rel_V(host(Hp), P.hessvec(lin, p), Ks) < 1e-5
