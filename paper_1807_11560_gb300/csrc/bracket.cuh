@@ -99,13 +99,25 @@ __device__ __forceinline__ void ld2<float2>(const float2* p, float2& a, float2& 
   b = make_float2(v.z, v.w);
 }
 
+// asynchronous global -> shared copies (cp.async): a staging loop issues all of
+// its requests before the first one returns, so a phase pays one L2 round trip
+// for its inputs instead of one per loop iteration
+template <typename V>
+__device__ __forceinline__ void cp_async(V* dst, const V* src) {
+  static_assert(sizeof(V) == 4 || sizeof(V) == 8 || sizeof(V) == 16, "cp.async size");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(sizeof(V)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __host__ __device__ __forceinline__ int even_up(int n) { return n + (n & 1); }
 __host__ __device__ __forceinline__ int quad_up(int n) { return (n + 3) & ~3; }
 
 // ---------------------------------------------------------------------------
 // iota stages A + B of one slab, in 2 x 2 complex register tiles.
-// Shared memory: S0 [K2][K3], S1 [K2][G3e], and with TWS the twiddles
-// E3 [K3][G3e] and E2 [K2][G2e] (G*e = even-rounded, zero padded).
+// Shared memory: S0 [K2][K3], S1 [K2][G3e], with TWS the twiddles
+// E3 [K3][G3e] and E2 [K2][G2e] (G*e = even-rounded, zero padded), then the
+// multiplier row sL [K2][K3].
 template <typename T, bool TWS>
 __device__ __forceinline__ void phase_iota_ab(const Plan<T>& p, const FieldSpec<T>& fs, int f, int h,
                                               const T* __restrict__ Lhat, cplx<T>* __restrict__ T2,
@@ -117,26 +129,33 @@ __device__ __forceinline__ void phase_iota_ab(const Plan<T>& p, const FieldSpec<
   C* S1 = S0 + K2 * K3;                      // [K2][G3e] after stage A
   C* E3s = S1 + K2 * G3e;                    // [K3][G3e]
   C* E2s = E3s + K3 * G3e;                   // [K2][G2e]
+  T* sL = reinterpret_cast<T*>(TWS ? E2s + K2 * G2e : E3s);   // [K2][K3]
   const int tid = threadIdx.x;
   const C zero{T(0), T(0)};
   if (TWS) {
     for (int i = tid; i < K3 * G3e; i += kThreads) {
       const int r = i / G3e, x = i - r * G3e;
-      E3s[i] = x < G3 ? p.E3f[r * G3 + x] : zero;
+      if (x < G3) cp_async(E3s + i, p.E3f + r * G3 + x); else E3s[i] = zero;
     }
     for (int i = tid; i < K2 * G2e; i += kThreads) {
       const int r = i / G2e, x = i - r * G2e;
-      E2s[i] = x < G2 ? p.E2f[r * G2 + x] : zero;
+      if (x < G2) cp_async(E2s + i, p.E2f + r * G2 + x); else E2s[i] = zero;
     }
   }
   const C* __restrict__ src = fs.src + (long long)h * K2 * K3;
   const T* __restrict__ Lrow = Lhat + (long long)h * K2 * K3;
   for (int i = tid; i < K2 * K3; i += kThreads) {
+    cp_async(S0 + i, src + i);
+    if (fs.applyL) cp_async(sL + i, Lrow + i);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int i = tid; i < K2 * K3; i += kThreads) {   // multiplier in place
     const int k2 = i / K3, k3 = i - k2 * K3;
     C a = zero;
     if (!nyq(k2, K2) && !nyq(k3, K3)) {
-      a = src[i];
-      if (fs.applyL) { const T l = Lrow[i]; a.x *= l; a.y *= l; }
+      a = S0[i];
+      if (fs.applyL) { const T l = sL[i]; a.x *= l; a.y *= l; }
       if (fs.deriv >= 0) {
         const T fr = fs.deriv == 0 ? T(h) : (fs.deriv == 1 ? T(sfreq(k2, K2)) : T(sfreq(k3, K3)));
         const T w = T(kTwoPi) * fr;
@@ -222,7 +241,8 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
   const C zero{T(0), T(0)};
 
   for (int fh = tid / TP, pp = tid - (tid / TP) * TP; fh < 24 * H1;) {
-    sT2[fh * TP + pp] = (p0 + pp < P) ? T2[(long long)fh * P + p0 + pp] : zero;
+    if (p0 + pp < P) cp_async(sT2 + fh * TP + pp, T2 + (long long)fh * P + p0 + pp);
+    else sT2[fh * TP + pp] = zero;
     pp += kThreads % TP;
     fh += kThreads / TP;
     if (pp >= TP) { pp -= TP; ++fh; }
@@ -247,12 +267,13 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
   }
   for (int i = tid; i < H1 * G1q; i += kThreads) {
     const int h = i / G1q, x = i - h * G1q;
-    sE1f[i] = x < G1 ? p.E1f[h * G1 + x] : zero;
+    if (x < G1) cp_async(sE1f + i, p.E1f + h * G1 + x); else sE1f[i] = zero;
   }
   for (int i = tid; i < G1 * H1q; i += kThreads) {
     const int x = i / H1q, h = i - x * H1q;
-    sE1b[i] = h < H1 ? p.E1b[x * H1 + h] : zero;
+    if (h < H1) cp_async(sE1b + i, p.E1b + x * H1 + h); else sE1b[i] = zero;
   }
+  cp_async_wait_all();
   __syncthreads();
   const int nq = G1q / 4;
   for (int it = tid; it < 24 * TP * nq; it += kThreads) {  // C: 24 grid fields, 4 planes each
@@ -374,11 +395,11 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
 
   for (int i = tid; i < G2 * KC; i += kThreads) {
     const int x2 = i / KC, kk = i - x2 * KC;
-    E2s[i] = kk < kc ? p.E2b[(long long)x2 * K2 + kb + kk] : zero;
+    if (kk < kc) cp_async(E2s + i, p.E2b + (long long)x2 * K2 + kb + kk); else E2s[i] = zero;
   }
   for (int i = tid; i < G3 * K3; i += kThreads) {
     const int x = i / K3, k = i - x * K3;
-    E3s[k * G3 + x] = p.E3b[i];
+    cp_async(E3s + k * G3 + x, p.E3b + i);
   }
   C acc[kAccB][kMaxKC];
 #pragma unroll
@@ -392,8 +413,9 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
     for (int o = 0; o < nper; ++o) {
       const C* __restrict__ src = P2 + (long long)((o * ncomp + c) * H1 + h) * P + (long long)x2c * G3;
       C* dst = slab + o * XB * G3;
-      for (int i = tid; i < xb * G3; i += kThreads) dst[i] = src[i];
+      for (int i = tid; i < xb * G3; i += kThreads) cp_async(dst + i, src + i);
     }
+    cp_async_wait_all();
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kAccB; ++r) {
@@ -456,28 +478,48 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
     const bool nq = nyq(k2, K2) || nyq(k3, K3);
     const long long kin = ((long long)h * K2 + k2) * K3 + k3;
     const long long at = (long long)c * kvol + kin;
-    // read every X term before any write: outputs may alias inputs
+    // read every X term before any write: outputs may alias inputs.  The loops
+    // run to the compile-time maxima with predicates so that the terms stay in
+    // registers and the loads issue together.
     C xs[kMaxOut][kMaxX];
-    for (int j = 0; j < nout; ++j)
-      for (int q = 0; q < e.nx[j]; ++q) xs[j][q] = e.X[j][q][at];
+#pragma unroll
+    for (int j = 0; j < kMaxOut; ++j)
+#pragma unroll
+      for (int q = 0; q < kMaxX; ++q) xs[j][q] = (j < nout && q < e.nx[j]) ? e.X[j][q][at] : zero;
     const T kh = T(1) / Lhat[kin];
-    C R[2] = {zero, zero};
+    C R0 = zero, R1 = zero;
     if (!nq) {
-      for (int o = 0; o < nper; ++o) {
-        const C y = Y[it * nper + o];
-        const T sc = e.coef[o] * (e.applyK[o] ? kh : T(1));
-        R[e.grp[o]].x += sc * y.x;
-        R[e.grp[o]].y += sc * y.y;
+#pragma unroll
+      for (int o = 0; o < kMaxPer; ++o) {
+        if (o < nper) {
+          const C y = Y[it * nper + o];
+          const T sc = e.coef[o] * (e.applyK[o] ? kh : T(1));
+          if (e.grp[o] == 0) {
+            R0.x += sc * y.x;
+            R0.y += sc * y.y;
+          } else {
+            R1.x += sc * y.x;
+            R1.y += sc * y.y;
+          }
+        }
       }
     }
     C val[kMaxOut];
-    for (int j = 0; j < nout; ++j) {
+#pragma unroll
+    for (int j = 0; j < kMaxOut; ++j) {
       C v = zero;
-      if (!nq) {
-        if (e.r[j] >= 0) { v.x = e.cR[j] * R[e.r[j]].x; v.y = e.cR[j] * R[e.r[j]].y; }
-        for (int q = 0; q < e.nx[j]; ++q) {
-          v.x += e.cX[j][q] * xs[j][q].x;
-          v.y += e.cX[j][q] * xs[j][q].y;
+      if (j < nout && !nq) {
+        if (e.r[j] >= 0) {
+          const C Rj = e.r[j] == 0 ? R0 : R1;
+          v.x = e.cR[j] * Rj.x;
+          v.y = e.cR[j] * Rj.y;
+        }
+#pragma unroll
+        for (int q = 0; q < kMaxX; ++q) {
+          if (q < e.nx[j]) {
+            v.x += e.cX[j][q] * xs[j][q].x;
+            v.y += e.cX[j][q] * xs[j][q].y;
+          }
         }
       }
       val[j] = v;
@@ -485,7 +527,9 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
     const long long mir = (long long)c * kvol +
         (((long long)((K1 - h) % K1) * K2 + (K2 - k2) % K2) * K3 + (K3 - k3) % K3);
     const long long nyq1 = (long long)c * kvol + (((long long)(K1 / 2) * K2 + k2) * K3 + k3);
-    for (int j = 0; j < nout; ++j) {
+#pragma unroll
+    for (int j = 0; j < kMaxOut; ++j) {
+      if (j >= nout) break;
       e.dst[j][at] = val[j];
       if (h > 0) e.dst[j][mir] = C{val[j].x, -val[j].y};
       if (h == 0 && K1 % 2 == 0) e.dst[j][nyq1] = zero;
@@ -500,7 +544,7 @@ __host__ __device__ inline size_t ab_smem(const Plan<T>& p, bool tws) {
   const size_t G2e = even_up(p.g.n2), G3e = even_up(p.g.n3);
   size_t n = (size_t)p.b.k2 * p.b.k3 + (size_t)p.b.k2 * G3e;
   if (tws) n += (size_t)p.b.k3 * G3e + (size_t)p.b.k2 * G2e;
-  return n * sizeof(cplx<T>);
+  return n * sizeof(cplx<T>) + (size_t)p.b.k2 * p.b.k3 * sizeof(T);
 }
 
 // stage the twiddles only while the tile stays small enough for several CTAs

@@ -64,6 +64,10 @@ template <typename T, int MODE, bool TWS>
 __global__ void __launch_bounds__(kThreads)
 k_sweep(SweepArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  // the current evaluation's descriptor, staged once per evaluation: the
+  // epilogue indexes its pointer and coefficient tables many times
+  __shared__ __align__(16) EvalDesc<T> sev;
+  static_assert(sizeof(EvalDesc<T>) % sizeof(unsigned long long) == 0, "descriptor size");
   const Plan<T>& p = a.p;
   const int H1 = p.b.h1;
   const long long P = (long long)p.g.n2 * p.g.n3;
@@ -73,7 +77,14 @@ k_sweep(SweepArgs<T> a) {
   const int n_ba = 3 * H1 * a.ba.nch;
   unsigned target = 0;
   for (int ev = 0; ev < a.nev; ++ev) {
-    const EvalDesc<T>* E = a.ev + ev;
+    {
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(a.ev + ev);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sev);
+      for (int i = threadIdx.x; i < (int)(sizeof(EvalDesc<T>) / sizeof(unsigned long long)); i += kThreads)
+        dst[i] = src[i];
+      __syncthreads();
+    }
+    const EvalDesc<T>* E = &sev;
     const cplx<T>* A = E->srcA;
     const cplx<T>* B = E->srcB;
     T* slot = E->slot;
