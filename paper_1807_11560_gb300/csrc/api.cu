@@ -50,7 +50,7 @@ template <typename T>
 struct State {
   cplx<T>* vh = nullptr;    // [Nt+1][3][Kvol]
   cplx<T>* vsh = nullptr;   // [Nt][3][Kvol]
-  T* cache = nullptr;       // [2 Nt][24][Mvol]
+  T* cache = nullptr;       // [2 Nt][cache_slot_elems]: 24 padded-grid fields per stage point
   T* vgrid = nullptr;       // [Nt+1][3][Nvol]
   T* mh = nullptr;          // [Nt+1][Nvol]
   T* off = nullptr;         // [Nt][3][Nvol]
@@ -192,7 +192,7 @@ struct Impl {
   void make_state(State<T>& S) {
     alloc(S.vh, (size_t)(Nt + 1) * 3 * Kvol);
     alloc(S.vsh, (size_t)Nt * 3 * Kvol);
-    alloc(S.cache, (size_t)2 * Nt * 24 * Mvol);
+    alloc(S.cache, (size_t)2 * Nt * cache_slot_elems<T>(pad));
     alloc(S.vgrid, (size_t)(Nt + 1) * 3 * Nvol);
     alloc(S.mh, (size_t)(Nt + 1) * Nvol);
     alloc(S.off, (size_t)Nt * 3 * Nvol);
@@ -261,7 +261,7 @@ struct Impl {
     alloc(dres, 8);
     cuda(cudaMemset(dres, 0, 8 * sizeof(double)), "memset");
     cuda(cudaMallocHost(&hres, 8 * sizeof(double)), "cudaMallocHost");
-    alloc(bar, 2);
+    alloc(bar, kSweepBarWords);
     record_sweeps();
     cuda(cudaDeviceSynchronize(), "create");
   }
@@ -517,7 +517,7 @@ struct Impl {
   }
 
   // ------------------------------------------------------------- sweeps
-  T* slot(State<T>& S, int k) { return S.cache + (long long)k * 24 * Mvol; }
+  T* slot(State<T>& S, int k) { return S.cache + (long long)k * cache_slot_elems<T>(pad); }
   C* vec(C* base, int n) { return base + (long long)n * 3 * Kvol; }
 
   // Heun shoot of BL EPDiff (Eq. 51); S.vh[0] must hold v0

@@ -54,6 +54,12 @@ __device__ __forceinline__ FieldSpec<T> field24(const cplx<T>* A, const cplx<T>*
   return FieldSpec<T>{s + ((g - 3) / 3) * kvol, (g - 3) % 3, L};
 }
 
+// velocity component whose band slab field f of a 24-field block reads
+__host__ __device__ __forceinline__ int field24_comp(int f) {
+  const int g = f >= 12 ? f - 12 : f;
+  return g < 3 ? g : (g - 3) / 3;
+}
+
 // ---------------------------------------------------------------------------
 // bracket products on one grid point
 // P(a, m)_i = sum_j Da[j][i] m_j + sum_j Dm[i][j] a_j + m_i div a   (ad* bracket, Eq. 4)
@@ -248,20 +254,22 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
     if (pp >= TP) { pp -= TP; ++fh; }
   }
   // the cached stage-point fields of this thread's (up to 2) product points,
-  // fetched now so their latency overlaps the transform stage
-  const long long fs = (long long)G1 * P;                  // field stride of a slot
+  // fetched now so their latency overlaps the transform stage.  The slot is
+  // tile-major, [tile][24][G1][TP] (the layout of sG), so these loads are
+  // contiguous across the threads of a warp.
+  T* __restrict__ tslot = slot + (long long)vb * 24 * G1 * TP;
   T cv[2][12], cl[2][12];
   if (MODE != PW_F) {
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const int i = tid + r * kThreads;
-      const int x1 = i / TP, pp = i - (i / TP) * TP;
+      const int pp = i - (i / TP) * TP;
       const bool ok = i < G1 * TP && p0 + pp < P;
-      const T* __restrict__ cs = slot + (long long)x1 * P + p0 + pp;
+      const T* __restrict__ cs = tslot + i;
 #pragma unroll
       for (int f = 0; f < 12; ++f) {
-        cv[r][f] = ok ? cs[f * fs] : T(0);
-        cl[r][f] = ok ? cs[(12 + f) * fs] : T(0);
+        cv[r][f] = ok ? cs[f * G1 * TP] : T(0);
+        cl[r][f] = ok ? cs[(12 + f) * G1 * TP] : T(0);
       }
     }
   }
@@ -299,7 +307,7 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
       const int x1 = x0 + t;
       if (x1 < G1) {
         sG[(f * G1 + x1) * TP + pp] = vv[t];
-        if (MODE == PW_F && p0 + pp < P) slot[f * fs + (long long)x1 * P + p0 + pp] = vv[t];
+        if (MODE == PW_F) tslot[(f * G1 + x1) * TP + pp] = vv[t];
       }
     }
   }
@@ -363,12 +371,17 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
 // ---------------------------------------------------------------------------
 // pi B' + A' + epilogue for (component c, h, k2 chunk of kc <= kMaxKC rows).
 // B' streams the P2 slab of every product field of c in chunks of XB rows of
-// x2 through shared memory; a thread owns up to kAccB (field, x3) columns and
-// accumulates all kc rows of each.  A' splits every band-slot sum over kRed
-// lanes and reduces with shuffles.
+// x2 through shared memory; a (virtual) thread owns one (field, x3) column and
+// accumulates the kc band rows of every R-th x2 row (R row groups use the
+// threads a narrow slab would leave idle; their partial sums are added in
+// fixed order).  A' splits every band-slot sum over kRed lanes and reduces
+// with shuffles.  The epilogue's inputs (the X terms and L^ of every band
+// slot) are prefetched with the slab.
 constexpr int kMaxKC = 8;
+constexpr int kMaxRows = 8;   // row groups R of B'
+constexpr int kEpiX = kMaxOut * kMaxX;
 struct BAGeom {
-  int KC, nch, XB;
+  int KC, nch, XB, R;
 };
 
 template <typename T>
@@ -377,19 +390,23 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
                                             unsigned char* smraw) {
   using C = cplx<T>;
   const int G2 = p.g.n2, G3 = p.g.n3, K1 = p.b.k1, K2 = p.b.k2, K3 = p.b.k3, H1 = p.b.h1;
-  const int KC = g.KC, nch = g.nch, XB = g.XB;
+  const int KC = g.KC, nch = g.nch, XB = g.XB, R = g.R;
   const long long P = (long long)G2 * G3;
   const long long kvol = (long long)K1 * K2 * K3;
   const int nper = e.nper, ncomp = e.ncomp, nout = e.nout;
+  const int ncol = nper * G3;
   C* slab = reinterpret_cast<C*>(smraw);                   // [nper][XB][G3]
   C* E2s = slab + nper * XB * G3;                          // [G2][KC]
   C* E3s = E2s + G2 * KC;                                  // [K3][G3] (transposed E3b)
-  C* S1 = E3s + G3 * K3;                                   // [nper][KC][G3]
+  C* S1 = E3s + G3 * K3;                                   // [R][nper][KC][G3] (part 0: the sums)
+  C* sX = S1 + R * nper * KC * G3;                         // [KC K3][kEpiX] epilogue terms
+  T* sLh = reinterpret_cast<T*>(sX + KC * K3 * kEpiX);     // [KC K3] L^ of the band slots
   const int chunk = vb % nch;
   const int h = (vb / nch) % H1;
   const int c = vb / (nch * H1);
   const int kb = chunk * KC;
   const int kc = min(KC, K2 - kb);
+  const int nslot = kc * K3;
   const int tid = threadIdx.x;
   const C zero{T(0), T(0)};
 
@@ -401,12 +418,25 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
     const int x = i / K3, k = i - x * K3;
     cp_async(E3s + k * G3 + x, p.E3b + i);
   }
+  for (int i = tid; i < nslot * kEpiX; i += kThreads) {
+    const int it = i / kEpiX, jq = i - it * kEpiX;
+    const int j = jq / kMaxX, q = jq - j * kMaxX;
+    if (j < nout && q < e.nx[j]) {
+      const int kk = it / K3, k3 = it - kk * K3;
+      const long long at = (long long)c * kvol + ((long long)h * K2 + kb + kk) * K3 + k3;
+      cp_async(sX + i, e.X[j][q] + at);
+    }
+  }
+  for (int it = tid; it < nslot; it += kThreads) {
+    const int kk = it / K3, k3 = it - kk * K3;
+    cp_async(sLh + it, Lhat + ((long long)h * K2 + kb + kk) * K3 + k3);
+  }
+
   C acc[kAccB][kMaxKC];
 #pragma unroll
   for (int r = 0; r < kAccB; ++r)
 #pragma unroll
     for (int kk = 0; kk < kMaxKC; ++kk) acc[r][kk] = zero;
-  const int ncol = nper * G3;
   for (int x2c = 0; x2c < G2; x2c += XB) {
     const int xb = min(XB, G2 - x2c);
     if (x2c > 0) __syncthreads();
@@ -419,11 +449,12 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kAccB; ++r) {
-      const int col = tid + r * kThreads;
-      if (col < ncol) {
+      const int vt = tid + r * kThreads;
+      const int part = vt / ncol, col = vt - part * ncol;
+      if (part < R) {
         const int o = col / G3, x3 = col - o * G3;
         const C* sl = slab + o * XB * G3 + x3;
-        for (int xr = 0; xr < xb; ++xr) {
+        for (int xr = ((part - x2c) % R + R) % R; xr < xb; xr += R) {
           const C a = sl[xr * G3];
           const C* er = E2s + (x2c + xr) * KC;
 #pragma unroll
@@ -435,19 +466,33 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
   }
 #pragma unroll
   for (int r = 0; r < kAccB; ++r) {
-    const int col = tid + r * kThreads;
-    if (col < ncol) {
+    const int vt = tid + r * kThreads;
+    const int part = vt / ncol, col = vt - part * ncol;
+    if (part < R) {
       const int o = col / G3, x3 = col - o * G3;
+      C* Sp = S1 + part * nper * KC * G3;
 #pragma unroll
       for (int kk = 0; kk < kMaxKC; ++kk)
-        if (kk < kc) S1[(o * KC + kk) * G3 + x3] = acc[r][kk];
+        if (kk < kc) Sp[(o * KC + kk) * G3 + x3] = acc[r][kk];
     }
   }
   __syncthreads();
+  if (R > 1) {                                             // add the row groups in fixed order
+    const int n1 = nper * KC * G3;
+    for (int i = tid; i < n1; i += kThreads) {
+      C a = S1[i];
+      for (int part = 1; part < R; ++part) {
+        const C b = S1[part * n1 + i];
+        a.x += b.x;
+        a.y += b.y;
+      }
+      S1[i] = a;
+    }
+    __syncthreads();
+  }
 
   // A': kRed consecutive lanes share one band-slot sum; the sums of every
   // product field go to shared memory (Y [nslot][nper], over the slab area)
-  const int nslot = kc * K3;
   C* Y = slab;                                             // slab no longer read (synced above)
   for (int base = 0; base < nslot * kRed; base += kThreads) {
     const int lin = base + tid;
@@ -471,69 +516,49 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
     }
   }
   __syncthreads();
-  // epilogue: one band slot per thread, every global load of a slot issued at once
-  for (int it = tid; it < nslot; it += kThreads) {
+  // epilogue: one (band slot, output) pair per thread; the X terms were read
+  // into shared memory before any output was written (outputs may alias inputs)
+  for (int w = tid; w < nslot * nout; w += kThreads) {
+    const int it = w / nout, j = w - it * nout;
     const int kk = it / K3, k3 = it - kk * K3;
     const int k2 = kb + kk;
     const bool nq = nyq(k2, K2) || nyq(k3, K3);
     const long long kin = ((long long)h * K2 + k2) * K3 + k3;
     const long long at = (long long)c * kvol + kin;
-    // read every X term before any write: outputs may alias inputs.  The loops
-    // run to the compile-time maxima with predicates so that the terms stay in
-    // registers and the loads issue together.
-    C xs[kMaxOut][kMaxX];
-#pragma unroll
-    for (int j = 0; j < kMaxOut; ++j)
-#pragma unroll
-      for (int q = 0; q < kMaxX; ++q) xs[j][q] = (j < nout && q < e.nx[j]) ? e.X[j][q][at] : zero;
-    const T kh = T(1) / Lhat[kin];
-    C R0 = zero, R1 = zero;
+    C v = zero;
     if (!nq) {
+      if (e.r[j] >= 0) {
+        const T kh = T(1) / sLh[it];
+        C Rj = zero;
 #pragma unroll
-      for (int o = 0; o < kMaxPer; ++o) {
-        if (o < nper) {
-          const C y = Y[it * nper + o];
-          const T sc = e.coef[o] * (e.applyK[o] ? kh : T(1));
-          if (e.grp[o] == 0) {
-            R0.x += sc * y.x;
-            R0.y += sc * y.y;
-          } else {
-            R1.x += sc * y.x;
-            R1.y += sc * y.y;
+        for (int o = 0; o < kMaxPer; ++o) {
+          if (o < nper && e.grp[o] == e.r[j]) {
+            const C y = Y[it * nper + o];
+            const T sc = e.coef[o] * (e.applyK[o] ? kh : T(1));
+            Rj.x += sc * y.x;
+            Rj.y += sc * y.y;
           }
+        }
+        v.x = e.cR[j] * Rj.x;
+        v.y = e.cR[j] * Rj.y;
+      }
+      const C* xs = sX + it * kEpiX + j * kMaxX;
+#pragma unroll
+      for (int q = 0; q < kMaxX; ++q) {
+        if (q < e.nx[j]) {
+          const C x = xs[q];
+          v.x += e.cX[j][q] * x.x;
+          v.y += e.cX[j][q] * x.y;
         }
       }
     }
-    C val[kMaxOut];
-#pragma unroll
-    for (int j = 0; j < kMaxOut; ++j) {
-      C v = zero;
-      if (j < nout && !nq) {
-        if (e.r[j] >= 0) {
-          const C Rj = e.r[j] == 0 ? R0 : R1;
-          v.x = e.cR[j] * Rj.x;
-          v.y = e.cR[j] * Rj.y;
-        }
-#pragma unroll
-        for (int q = 0; q < kMaxX; ++q) {
-          if (q < e.nx[j]) {
-            v.x += e.cX[j][q] * xs[j][q].x;
-            v.y += e.cX[j][q] * xs[j][q].y;
-          }
-        }
-      }
-      val[j] = v;
+    e.dst[j][at] = v;
+    if (h > 0) {
+      const long long mir = (long long)c * kvol +
+          (((long long)((K1 - h) % K1) * K2 + (K2 - k2) % K2) * K3 + (K3 - k3) % K3);
+      e.dst[j][mir] = C{v.x, -v.y};
     }
-    const long long mir = (long long)c * kvol +
-        (((long long)((K1 - h) % K1) * K2 + (K2 - k2) % K2) * K3 + (K3 - k3) % K3);
-    const long long nyq1 = (long long)c * kvol + (((long long)(K1 / 2) * K2 + k2) * K3 + k3);
-#pragma unroll
-    for (int j = 0; j < kMaxOut; ++j) {
-      if (j >= nout) break;
-      e.dst[j][at] = val[j];
-      if (h > 0) e.dst[j][mir] = C{val[j].x, -val[j].y};
-      if (h == 0 && K1 % 2 == 0) e.dst[j][nyq1] = zero;
-    }
+    if (h == 0 && K1 % 2 == 0) e.dst[j][(long long)c * kvol + (((long long)(K1 / 2) * K2 + k2) * K3 + k3)] = zero;
   }
 }
 
@@ -570,27 +595,37 @@ inline int cpw_tile(const Plan<T>& p) {
   return TP;
 }
 
+
+template <typename T>
+inline size_t ba_smem(const Plan<T>& p, int nper, const BAGeom& g) {
+  const size_t G2 = p.g.n2, G3 = p.g.n3, K3 = p.b.k3, KC = g.KC;
+  return ((size_t)nper * g.XB * G3 + G2 * KC + G3 * K3 + (size_t)g.R * nper * KC * G3 + KC * K3 * kEpiX) *
+             sizeof(cplx<T>) +
+         KC * K3 * sizeof(T);
+}
+
 template <typename T>
 inline BAGeom ba_geom(const Plan<T>& p, int ncomp, int nper) {
-  const int G2 = p.g.n2, G3 = p.g.n3, K2 = p.b.k2, K3 = p.b.k3;
+  const int G2 = p.g.n2, G3 = p.g.n3, K2 = p.b.k2;
   const int groups = ncomp * p.b.h1;
   const int want = std::max(1, (304 + groups - 1) / groups);
   int KC = std::max(1, (K2 + want - 1) / want);
   KC = std::min(std::min(KC, kMaxKC), K2);
-  const int nch = (K2 + KC - 1) / KC;
-  const size_t c = sizeof(cplx<T>);
-  const size_t fixed = ((size_t)G2 * KC + (size_t)G3 * K3 + (size_t)nper * KC * G3) * c;
-  const size_t budget = fixed < (size_t)kMaxSmem ? (size_t)kMaxSmem - fixed : 0;
-  const size_t rows = std::min<size_t>(budget, 96 * 1024) / ((size_t)nper * G3 * c);
-  // the slab area later holds the A' sums of kc * K3 slots: XB >= KC suffices (G3 >= K3)
-  const int XB = std::max(KC, (int)std::min<size_t>((size_t)G2, std::max<size_t>(1, rows)));
-  return BAGeom{KC, nch, XB};
-}
-
-template <typename T>
-inline size_t ba_smem(const Plan<T>& p, int nper, const BAGeom& g) {
-  return ((size_t)nper * g.XB * p.g.n3 + (size_t)p.g.n2 * g.KC + (size_t)p.g.n3 * p.b.k3 +
-          (size_t)nper * g.KC * p.g.n3) * sizeof(cplx<T>);
+  const int ncol = nper * G3;
+  const int R = std::max(1, std::min(kMaxRows, kThreads / ncol));
+  BAGeom g{KC, (K2 + KC - 1) / KC, 1, R};
+  const size_t row = (size_t)nper * G3 * sizeof(cplx<T>);
+  auto fixed = [&]() { return ba_smem(p, nper, g) - row; };    // all but the slab rows
+  // the slab area later holds the A' sums of kc * K3 slots, so XB >= KC (G3 >= K3)
+  while (g.KC > 1 && fixed() + row * g.KC > (size_t)kMaxSmem) {
+    --g.KC;
+    g.nch = (K2 + g.KC - 1) / g.KC;
+  }
+  // slab rows: as many as keep the CTA within 72 KB (three CTAs per SM)
+  const size_t target = 72 * 1024;
+  const size_t rows = fixed() < target ? (target - fixed()) / row : 0;
+  g.XB = std::max(g.KC, (int)std::min<size_t>((size_t)G2, rows));
+  return g;
 }
 
 }  // namespace dev

@@ -179,6 +179,13 @@ size_t max_smem_needed(const Plan<T>& p, int nper_max, bool brackets) {
 
 size_t smem_limit() { return kMaxSmem; }
 
+template <typename T>
+long long cache_slot_elems(const Plan<T>& p) {
+  const long long P = (long long)p.g.n2 * p.g.n3;
+  const int TP = dev::cpw_tile(p);
+  return 24LL * p.g.n1 * TP * ((P + TP - 1) / TP);
+}
+
 // register slots of the image-grid C / C' kernels: the smallest of 8/16/32 >= K1/2
 template <typename T, int HR>
 void launch_C(const Plan<T>& p, const IotaDesc<T>& d, const cplx<T>* T2, unsigned grid, size_t smem,
@@ -263,6 +270,7 @@ void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T
 
 #define LDDMM_DFT_INST(T)                                                                          \
   template size_t max_smem_needed<T>(const Plan<T>&, int, bool);                                   \
+  template long long cache_slot_elems<T>(const Plan<T>&);                                           \
   template void iota_batch<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t,    \
                               double*);                                                            \
   template void pi_batch<T>(const Plan<T>&, const PiSrc<T>&, const PiEpi<T>&, const T*, cplx<T>*,  \

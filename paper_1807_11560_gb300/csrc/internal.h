@@ -139,9 +139,11 @@ struct EvalDesc {
   PiEpi<T> epi;
 };
 // Every evaluation of a band-limited sweep in one cooperative launch
-// (sweep.cu); ev is a device array of nev descriptors of one mode.  bar: two
-// device unsigned ints of barrier state; flag: device double set to 1 if a
-// barrier wait gave up.
+// (sweep.cu); ev is a device array of nev descriptors of one mode.  bar:
+// kSweepBarWords device unsigned ints of barrier state (the grid-barrier
+// arrival counter and one completion counter per (component, h) band slab);
+// flag: device double set to 1 if a wait gave up.
+constexpr int kSweepBarWords = 128;
 template <typename T>
 cudaError_t sweep_launch(const Plan<T>& p, PwMode mode, const EvalDesc<T>* ev, int nev, const T* Lhat,
                          cplx<T>* T2, cplx<T>* P2, unsigned* bar, double* flag, cudaStream_t st);
@@ -153,6 +155,11 @@ cudaError_t sweep_launch(const Plan<T>& p, PwMode mode, const EvalDesc<T>* ev, i
 template <typename T>
 size_t max_smem_needed(const Plan<T>& p, int nper_max, bool brackets);
 size_t smem_limit();
+// floats of one stage-point cache slot of a bracket evaluation: the 24 grid
+// fields of every pencil tile of the C/products/C' phase, tile-major
+// [tile][24][M1][TP] so that a tile's fields are one contiguous block
+template <typename T>
+long long cache_slot_elems(const Plan<T>& p);
 
 // ---- grid kernels (grid.cu) -----------------------------------------------
 // Semi-Lagrangian state step (Eq. 52): m_next(x) = m(X_n(x)), foot point from

@@ -5,9 +5,16 @@
 // At small grids the phases last a few microseconds each, so removing the
 // kernel boundaries between them is what bounds the sweep time.
 //
-// Barrier waits are bounded: a CTA that spins longer than the limit records
-// the failure in a flag the host reads (LDDMM_ETIMEOUT) and every CTA leaves
-// at its next barrier.  The launch is cooperative, so all CTAs are resident.
+// Between the pi phase of one evaluation and the iota phase of the next there
+// is no grid barrier: the iota item of (field f, h) reads only the band slab
+// (component of f, h), so it waits for the completion counter of that slab
+// (bumped by each pi item of the slab) instead of for the whole grid.  The
+// other two phase boundaries are all-to-all (transposes) and keep barriers.
+//
+// Waits are bounded: a CTA that spins longer than the limit records the
+// failure in a flag the host reads (LDDMM_ETIMEOUT) and every CTA leaves at
+// its next barrier or wait.  The launch is cooperative, so all CTAs are
+// resident, and no CTA waits on an item that comes after its own wait.
 #include "bracket.cuh"
 
 namespace lddmm {
@@ -28,7 +35,7 @@ struct SweepArgs {
   int nev;
   int TP;                     // pencil tile of the C/products/C' phase
   dev::BAGeom ba;             // geometry of the pi B'/A' phase
-  unsigned* bar;              // [0] arrival counter
+  unsigned* bar;              // [0] arrival counter, [1 + c H1 + h] slab completion counters
   double* flag;               // set to 1 when a barrier wait gives up
 };
 
@@ -50,6 +57,31 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& target, 
     atomicAdd(count, 1u);
     long long it = 0;
     while (load_acquire(count) < target) {
+      if (++it > kSpinLimit) {
+        *(volatile double*)flag = 1.0;
+        break;
+      }
+    }
+    if (*(volatile double*)flag != 0.0) ok = 0;
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// publish the completion of one pi item: its writes, then the counter
+__device__ __forceinline__ void signal_slab(unsigned* cnt) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(cnt, 1u);
+  }
+}
+
+// wait until a slab completion counter reaches target (acquire), bounded
+__device__ __forceinline__ bool wait_slab(const unsigned* cnt, unsigned target, double* flag) {
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    long long it = 0;
+    while (load_acquire(cnt) < target) {
       if (++it > kSpinLimit) {
         *(volatile double*)flag = 1.0;
         break;
@@ -90,7 +122,10 @@ k_sweep(SweepArgs<T> a) {
     T* slot = E->slot;
     for (int vb = blockIdx.x; vb < n_ab; vb += gridDim.x) {
       const int f = vb / H1, h = vb % H1;
-      dev::phase_iota_ab<T, TWS>(p, dev::field24<T>(A, B, kvol, f), f, h, a.Lhat, a.T2, smraw);
+      const dev::FieldSpec<T> fs = dev::field24<T>(A, B, kvol, f);
+      if (ev > 0 && !wait_slab(a.bar + 1 + dev::field24_comp(f) * H1 + h, (unsigned)(a.ba.nch * ev), a.flag))
+        return;
+      dev::phase_iota_ab<T, TWS>(p, fs, f, h, a.Lhat, a.T2, smraw);
       __syncthreads();
     }
     if (!grid_barrier(a.bar, target, a.flag)) return;
@@ -101,9 +136,10 @@ k_sweep(SweepArgs<T> a) {
     if (!grid_barrier(a.bar, target, a.flag)) return;
     for (int vb = blockIdx.x; vb < n_ba; vb += gridDim.x) {
       dev::phase_pi_ba<T>(p, E->epi, a.Lhat, a.P2, a.ba, vb, smraw);
-      __syncthreads();
+      const int h = (vb / a.ba.nch) % H1, c = vb / (a.ba.nch * H1);
+      signal_slab(a.bar + 1 + c * H1 + h);
     }
-    if (!grid_barrier(a.bar, target, a.flag)) return;
+    __syncthreads();
   }
 }
 
@@ -161,7 +197,8 @@ cudaError_t sweep_launch(const Plan<T>& p, PwMode mode, const EvalDesc<T>* ev, i
   const long long P = (long long)p.g.n2 * p.g.n3;
   const int max_ctas = (int)std::max<long long>(
       24LL * p.b.h1, std::max<long long>((P + a.TP - 1) / a.TP, 3LL * p.b.h1 * a.ba.nch));
-  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
+  if (1 + 3 * p.b.h1 > kSweepBarWords) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(bar, 0, kSweepBarWords * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   switch (mode) {
     case PW_F: return dispatch_tws<T, PW_F>(a, smem, tws, st, max_ctas);
