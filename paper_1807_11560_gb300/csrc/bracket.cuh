@@ -116,6 +116,20 @@ __device__ __forceinline__ void cp_async(V* dst, const V* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// n contiguous elements, copied by all threads of the CTA: 16-byte requests
+// when both ends allow it, else one request per element
+template <typename V>
+__device__ __forceinline__ void cp_async_run(V* dst, const V* src, int n) {
+  constexpr int per = 16 / (int)sizeof(V);
+  if (per > 1 && n % per == 0 && ((reinterpret_cast<size_t>(dst) | reinterpret_cast<size_t>(src)) & 15) == 0) {
+    float4* d = reinterpret_cast<float4*>(dst);
+    const float4* q = reinterpret_cast<const float4*>(src);
+    for (int i = threadIdx.x; i < n / per; i += kThreads) cp_async(d + i, q + i);
+  } else {
+    for (int i = threadIdx.x; i < n; i += kThreads) cp_async(dst + i, src + i);
+  }
+}
+
 __host__ __device__ __forceinline__ int even_up(int n) { return n + (n & 1); }
 __host__ __device__ __forceinline__ int quad_up(int n) { return (n + 3) & ~3; }
 
@@ -150,10 +164,8 @@ __device__ __forceinline__ void phase_iota_ab(const Plan<T>& p, const FieldSpec<
   }
   const C* __restrict__ src = fs.src + (long long)h * K2 * K3;
   const T* __restrict__ Lrow = Lhat + (long long)h * K2 * K3;
-  for (int i = tid; i < K2 * K3; i += kThreads) {
-    cp_async(S0 + i, src + i);
-    if (fs.applyL) cp_async(sL + i, Lrow + i);
-  }
+  cp_async_run(S0, src, K2 * K3);
+  if (fs.applyL) cp_async_run(sL, Lrow, K2 * K3);
   cp_async_wait_all();
   __syncthreads();
   for (int i = tid; i < K2 * K3; i += kThreads) {   // multiplier in place
@@ -180,6 +192,7 @@ __device__ __forceinline__ void phase_iota_ab(const Plan<T>& p, const FieldSpec<
     const int k2 = 2 * kp, x3 = 2 * xp;
     C c00 = zero, c01 = zero, c10 = zero, c11 = zero;
     const C* s0 = S0 + k2 * K3;
+#pragma unroll 4
     for (int k3 = 0; k3 < K3; ++k3) {
       const C a0 = s0[k3], a1 = s0[K3 + k3];
       C e0, e1;
@@ -204,6 +217,7 @@ __device__ __forceinline__ void phase_iota_ab(const Plan<T>& p, const FieldSpec<
     const int yp = it / n3p, xp = it - yp * n3p;
     const int x2 = 2 * yp, x3 = 2 * xp;
     C c00 = zero, c01 = zero, c10 = zero, c11 = zero;
+#pragma unroll 4
     for (int k2 = 0; k2 < K2; ++k2) {
       C s0, s1, e0, e1;
       ld2(S1 + k2 * G3e + x3, s0, s1);
@@ -291,6 +305,7 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
     const int x0 = 4 * xq;
     const C* s = sT2 + f * H1 * TP + pp;
     T v0 = T(0), v1 = T(0), v2 = T(0), v3 = T(0);
+#pragma unroll 4
     for (int h = 0; h < H1; ++h) {
       const C a = s[h * TP];
       C e0, e1, e2, e3;
@@ -351,6 +366,7 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
     if (p0 + pp >= P) continue;
     const T* sp = sP + q * G1 * TP + pp;
     C a0 = zero, a1 = zero, a2 = zero, a3 = zero;
+#pragma unroll 4
     for (int x1 = 0; x1 < G1; ++x1) {
       const T v = sp[x1 * TP];
       C e0, e1, e2, e3;
@@ -442,8 +458,7 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
     if (x2c > 0) __syncthreads();
     for (int o = 0; o < nper; ++o) {
       const C* __restrict__ src = P2 + (long long)((o * ncomp + c) * H1 + h) * P + (long long)x2c * G3;
-      C* dst = slab + o * XB * G3;
-      for (int i = tid; i < xb * G3; i += kThreads) cp_async(dst + i, src + i);
+      cp_async_run(slab + o * XB * G3, src, xb * G3);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -454,6 +469,7 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
       if (part < R) {
         const int o = col / G3, x3 = col - o * G3;
         const C* sl = slab + o * XB * G3 + x3;
+#pragma unroll 4
         for (int xr = ((part - x2c) % R + R) % R; xr < xb; xr += R) {
           const C a = sl[xr * G3];
           const C* er = E2s + (x2c + xr) * KC;

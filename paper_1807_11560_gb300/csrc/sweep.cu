@@ -96,10 +96,12 @@ template <typename T, int MODE, bool TWS>
 __global__ void __launch_bounds__(kThreads)
 k_sweep(SweepArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  // the current evaluation's descriptor, staged once per evaluation: the
-  // epilogue indexes its pointer and coefficient tables many times
-  __shared__ __align__(16) EvalDesc<T> sev;
+  // evaluation descriptors in shared memory (the epilogue indexes their
+  // pointer and coefficient tables many times); the next one is fetched with
+  // cp.async while the current evaluation runs
+  __shared__ __align__(16) EvalDesc<T> sev[2];
   static_assert(sizeof(EvalDesc<T>) % sizeof(unsigned long long) == 0, "descriptor size");
+  constexpr int kDescWords = (int)(sizeof(EvalDesc<T>) / sizeof(unsigned long long));
   const Plan<T>& p = a.p;
   const int H1 = p.b.h1;
   const long long P = (long long)p.g.n2 * p.g.n3;
@@ -109,14 +111,19 @@ k_sweep(SweepArgs<T> a) {
   const int n_ba = 3 * H1 * a.ba.nch;
   unsigned target = 0;
   for (int ev = 0; ev < a.nev; ++ev) {
-    {
-      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(a.ev + ev);
-      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sev);
-      for (int i = threadIdx.x; i < (int)(sizeof(EvalDesc<T>) / sizeof(unsigned long long)); i += kThreads)
-        dst[i] = src[i];
-      __syncthreads();
+    if (ev == 0) {
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(a.ev);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sev[0]);
+      for (int i = threadIdx.x; i < kDescWords; i += kThreads) dst[i] = src[i];
     }
-    const EvalDesc<T>* E = &sev;
+    dev::cp_async_wait_all();                      // descriptor ev has landed
+    __syncthreads();
+    if (ev + 1 < a.nev) {
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(a.ev + ev + 1);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sev[(ev + 1) & 1]);
+      for (int i = threadIdx.x; i < kDescWords; i += kThreads) dev::cp_async(dst + i, src + i);
+    }
+    const EvalDesc<T>* E = &sev[ev & 1];
     const cplx<T>* A = E->srcA;
     const cplx<T>* B = E->srcB;
     T* slot = E->slot;
