@@ -90,6 +90,16 @@ typedef struct {
   int tensor_cores;     /* FP32 contexts: band-to-image-grid transforms (iota stage C) on
                            the tcgen05 tensor cores with the 3xTF32 split: 0 never,
                            1 for image grids of at least 2^20 voxels (default), 2 always */
+  int recompute;        /* image-grid histories of the time sweeps (velocity grids v_n,
+                           characteristic displacements, states m_n, incremental
+                           velocity grids): 0 keep all Nt + 1 steps (default); 1 keep
+                           two steps and regenerate the rest in forward time order where
+                           a sweep reads them (every reader runs forward in time, so no
+                           reverse-order checkpoints are needed).  Results are identical;
+                           the image-grid footprint drops from about 17 Nt + 20 to about 37
+                           floats per voxel (plus the transform scratch), and each
+                           Hessian-vector product re-runs the state transport (Nt steps
+                           and 2 (Nt + 1) vector iotas more). */
 } lddmm_opts;
 
 /* Report of lddmm_gn_solve.  The per-iteration arrays are optional
@@ -256,6 +266,10 @@ int lddmm_probe_read(lddmm_ctx* ctx, double* total_ms, long long* launches, doub
 /* Number of CUDA kernels this context has launched since creation (graph
  * replays count each kernel node). */
 long long lddmm_kernel_count(const lddmm_ctx* ctx);
+
+/* Bytes of device memory the context holds (all of it is allocated by
+ * lddmm_create; no later call allocates).  0 for NULL. */
+unsigned long long lddmm_device_bytes(const lddmm_ctx* ctx);
 
 /* One-line description of the last error on this context (never NULL). */
 const char* lddmm_last_error(const lddmm_ctx* ctx);

@@ -51,9 +51,9 @@ struct State {
   cplx<T>* vh = nullptr;    // [Nt+1][3][Kvol]
   cplx<T>* vsh = nullptr;   // [Nt][3][Kvol]
   T* cache = nullptr;       // [2 Nt][cache_slot_elems]: 24 padded-grid fields per stage point
-  T* vgrid = nullptr;       // [Nt+1][3][Nvol]
-  T* mh = nullptr;          // [Nt+1][Nvol]
-  T* off = nullptr;         // [Nt][3][Nvol]
+  T* vgrid = nullptr;       // [Nt+1][3][Nvol]  (recompute: [2][3][Nvol], step n in n & 1)
+  T* mh = nullptr;          // [Nt+1][Nvol]     (recompute: [2][Nvol])
+  T* off = nullptr;         // [Nt][3][Nvol]    (recompute: [3][Nvol], the current step)
 };
 
 template <typename T>
@@ -78,7 +78,7 @@ struct Impl {
     *W = nullptr, *dstar = nullptr, *vin = nullptr, *vout = nullptr, *gbuf = nullptr;
   C *px = nullptr, *pr = nullptr, *pd = nullptr, *pq = nullptr, *vsol = nullptr, *vtry = nullptr;
   C* dvh = nullptr;          // [Nt+1][3][Kvol]
-  T* dvgrid = nullptr;       // [Nt+1][3][Nvol]
+  T* dvgrid = nullptr;       // [Nt+1][3][Nvol]  (recompute: [2][3][Nvol])
   T *dm[2] = {nullptr, nullptr}, *sb[2] = {nullptr, nullptr};
   T* fterm = nullptr;        // [3][Nvol]
   double *partial = nullptr, *dres = nullptr;   // dres[7]: sweep barrier time-out flag
@@ -91,6 +91,7 @@ struct Impl {
   double sweep_flops[3] = {0, 0, 0};   // algorithmic flops of one sweep per mode
   long long launches = 0;
   std::vector<void*> allocs;
+  unsigned long long device_bytes = 0;
   // graph of one Hessian-vector product (input dvh[0], output vout)
   cudaGraphExec_t hv_exec = nullptr;
   long long hv_nodes = 0;
@@ -130,6 +131,7 @@ struct Impl {
       throw Fail{LDDMM_ENOMEM};
     }
     allocs.push_back(q);
+    device_bytes += bytes > 0 ? bytes : 16;
     p = static_cast<P_*>(q);
   }
   void release() {
@@ -193,10 +195,18 @@ struct Impl {
     alloc(S.vh, (size_t)(Nt + 1) * 3 * Kvol);
     alloc(S.vsh, (size_t)Nt * 3 * Kvol);
     alloc(S.cache, (size_t)2 * Nt * cache_slot_elems<T>(pad));
-    alloc(S.vgrid, (size_t)(Nt + 1) * 3 * Nvol);
-    alloc(S.mh, (size_t)(Nt + 1) * Nvol);
-    alloc(S.off, (size_t)Nt * 3 * Nvol);
+    const size_t steps = opts.recompute ? 2 : (size_t)Nt + 1;
+    alloc(S.vgrid, steps * 3 * Nvol);
+    alloc(S.mh, steps * Nvol);
+    alloc(S.off, (opts.recompute ? 1 : (size_t)Nt) * 3 * Nvol);
   }
+  // image-grid history accessors (step n of a kept or a two-step rolling history)
+  long long hstep(int n) const { return opts.recompute ? (n & 1) : n; }
+  T* mstate(State<T>& S, int n) { return S.mh + hstep(n) * Nvol; }
+  T* m1(State<T>& S) { return mstate(S, Nt); }
+  T* vgr(State<T>& S, int n) { return S.vgrid + hstep(n) * 3 * Nvol; }
+  T* offp(State<T>& S, int n) { return S.off + (opts.recompute ? 0 : (long long)n) * 3 * Nvol; }
+  T* dvg(int n) { return dvgrid + hstep(n) * 3 * Nvol; }
 
   void create(int nd, const int* grid, const int* band, double a, int s_, double sg, int nt,
               const lddmm_opts& o) {
@@ -251,7 +261,7 @@ struct Impl {
                   &vsol, &vtry})
       alloc(*b, (size_t)3 * Kvol);
     alloc(dvh, (size_t)(Nt + 1) * 3 * Kvol);
-    alloc(dvgrid, (size_t)(Nt + 1) * 3 * Nvol);
+    alloc(dvgrid, (opts.recompute ? 2 : (size_t)Nt + 1) * 3 * Nvol);
     for (int i = 0; i < 2; ++i) {
       alloc(dm[i], (size_t)Nvol);
       alloc(sb[i], (size_t)Nvol);
@@ -547,18 +557,29 @@ struct Impl {
     }
   }
 
+  // one semi-Lagrangian state step m_n -> m_{n+1} (Eq. 52) from the kept or
+  // regenerated velocity grids of steps n and n + 1
+  void state_step(State<T>& S, int n) {
+    pb(PR_TRANSPORT);
+    transport_step<T>(mstate(S, n), vgr(S, n + 1), vgr(S, n), mstate(S, n + 1), offp(S, n), N, dt, st);
+    pe(PR_TRANSPORT, 8.0 * (double)Nvol);
+    ++launches;
+  }
+
   // grid velocities and semi-Lagrangian transport of I0 (Eq. 52)
   void transport(State<T>& S) {
-    to_grid(S.vh, Nt + 1, S.vgrid);
-    cuda(cudaMemcpyAsync(S.mh, I0, (size_t)Nvol * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy I0");
-    for (int n = 0; n < Nt; ++n) {
-      pb(PR_TRANSPORT);
-      transport_step<T>(S.mh + n * Nvol, S.vgrid + (long long)(n + 1) * 3 * Nvol,
-                        S.vgrid + (long long)n * 3 * Nvol, S.mh + (n + 1) * Nvol,
-                        S.off + (long long)n * 3 * Nvol, N, dt, st);
-      pe(PR_TRANSPORT, 8.0 * (double)Nvol);
+    cuda(cudaMemcpyAsync(mstate(S, 0), I0, (size_t)Nvol * sizeof(T), cudaMemcpyDeviceToDevice, st),
+         "copy I0");
+    if (!opts.recompute) {
+      to_grid(S.vh, Nt + 1, S.vgrid);
+      for (int n = 0; n < Nt; ++n) state_step(S, n);
+    } else {
+      to_grid(S.vh, 1, vgr(S, 0));
+      for (int n = 0; n < Nt; ++n) {
+        to_grid(vec(S.vh, n + 1), 1, vgr(S, n + 1));
+        state_step(S, n);
+      }
     }
-    launches += Nt;
     check_launch("transport");
   }
 
@@ -570,7 +591,7 @@ struct Impl {
   // energy pieces into dres[0] (<v0,v0>_V) and dres[1] (sum (m1 - I1)^2)
   void energy_terms(State<T>& S) {
     inner_V<T>(S.vh, S.vh, Lhat, 3, Kvol, partial, dres, st);
-    sum_sq_diff<T>(S.mh + (long long)Nt * Nvol, I1, Nvol, partial, dres + 1, st);
+    sum_sq_diff<T>(m1(S), I1, Nvol, partial, dres + 1, st);
     launches += 4;
     check_launch("energy reductions");
   }
@@ -648,18 +669,29 @@ struct Impl {
   void enqueue_hessvec() {
     State<T>& S = lin;
     tangent(S);
-    to_grid(dvh, Nt + 1, dvgrid);
-    grad_dot<T>(S.mh, dvgrid, sb[0], N, st);
+    if (!opts.recompute) {
+      to_grid(dvh, Nt + 1, dvgrid);
+    } else {                                  // regenerate step 0 of the state history
+      cuda(cudaMemcpyAsync(mstate(S, 0), I0, (size_t)Nvol * sizeof(T), cudaMemcpyDeviceToDevice, st),
+           "copy I0");
+      to_grid(S.vh, 1, vgr(S, 0));
+      to_grid(dvh, 1, dvg(0));
+    }
+    grad_dot<T>(mstate(S, 0), dvg(0), sb[0], N, st);
     ++launches;
     for (int n = 0; n < Nt; ++n) {
+      if (opts.recompute) {                   // step n + 1 of the state and velocity histories
+        to_grid(vec(S.vh, n + 1), 1, vgr(S, n + 1));
+        to_grid(vec(dvh, n + 1), 1, dvg(n + 1));
+        state_step(S, n);
+      }
       pb(PR_INC);
-      inc_step<T>(n == 0 ? nullptr : dm[n & 1], sb[n & 1], S.mh + (long long)(n + 1) * Nvol,
-                  dvgrid + (long long)(n + 1) * 3 * Nvol, S.off + (long long)n * 3 * Nvol,
+      inc_step<T>(n == 0 ? nullptr : dm[n & 1], sb[n & 1], mstate(S, n + 1), dvg(n + 1), offp(S, n),
                   dm[(n + 1) & 1], sb[(n + 1) & 1], N, dt, st);
       pe(PR_INC, 12.0 * (double)Nvol);
     }
     launches += Nt;
-    terminal_field<T>(S.mh + (long long)Nt * Nvol, dm[Nt & 1], 0, -2.0 / (sigma * sigma), fterm, N, st);
+    terminal_field<T>(m1(S), dm[Nt & 1], 0, -2.0 / (sigma * sigma), fterm, N, st);
     ++launches;
     project_K(fterm, U);
     backward(S);
@@ -706,7 +738,7 @@ struct Impl {
          "copy v0");
     forward(lin);
     energy_terms(lin);
-    terminal_field<T>(lin.mh + (long long)Nt * Nvol, I1, 1, -2.0 / (sigma * sigma), fterm, N, st);
+    terminal_field<T>(m1(lin), I1, 1, -2.0 / (sigma * sigma), fterm, N, st);
     ++launches;
     project_K(fterm, U);
     backward(lin);
@@ -988,12 +1020,11 @@ struct Impl {
     check_flag(hres[7]);
   }
 
-  void transport_call(const void* v0, void* m1) {
+  void transport_call(const void* v0, void* m1out) {
     need_images();
     load_bl(v0, trial.vh);
     forward(trial);
-    cuda(cudaMemcpyAsync(m1, trial.mh + (long long)Nt * Nvol, (size_t)Nvol * sizeof(T),
-                         cudaMemcpyDefault, st), "copy m1");
+    cuda(cudaMemcpyAsync(m1out, m1(trial), (size_t)Nvol * sizeof(T), cudaMemcpyDefault, st), "copy m1");
     cuda(cudaMemcpyAsync(hres + 7, dres + 7, sizeof(double), cudaMemcpyDeviceToHost, st), "read flag");
     sync("transport");
     check_flag(hres[7]);
@@ -1008,7 +1039,7 @@ struct Impl {
     forward(lin);
     cuda(cudaMemcpyAsync(dm[0], gm1, (size_t)Nvol * sizeof(T), cudaMemcpyDefault, st), "copy grad m1");
     // lambda(1) = -N dL/dm(1): the L2_h adjoint of the grid values
-    terminal_field<T>(lin.mh + (long long)Nt * Nvol, dm[0], 0, -(double)Nvol, fterm, N, st);
+    terminal_field<T>(m1(lin), dm[0], 0, -(double)Nvol, fterm, N, st);
     ++launches;
     project_K(fterm, U);
     backward(lin);
@@ -1082,6 +1113,7 @@ void lddmm_default_opts(lddmm_opts* o) {
   o->use_graphs = 1;
   o->persistent = 1;
   o->tensor_cores = 1;
+  o->recompute = 0;
 }
 
 int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, double alpha, int s,
@@ -1246,6 +1278,12 @@ long long lddmm_kernel_count(const lddmm_ctx* ctx) {
   if (!ctx || !ctx->impl) return 0;
   if (ctx->precision == LDDMM_FP64) return static_cast<const Impl<double>*>(ctx->impl)->launches;
   return static_cast<const Impl<float>*>(ctx->impl)->launches;
+}
+
+unsigned long long lddmm_device_bytes(const lddmm_ctx* ctx) {
+  if (!ctx || !ctx->impl) return 0;
+  if (ctx->precision == LDDMM_FP64) return static_cast<const Impl<double>*>(ctx->impl)->device_bytes;
+  return static_cast<const Impl<float>*>(ctx->impl)->device_bytes;
 }
 
 const char* lddmm_last_error(const lddmm_ctx* ctx) {

@@ -31,7 +31,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("pcg_tol", ctypes.c_double), ("armijo_c", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("persistent", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
+                ("persistent", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("recompute", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -71,6 +72,7 @@ def lib():
         "lddmm_last_dm1": (I, [P, P]),
         "lddmm_transport_vjp": (I, [P, P, P, P]),
         "lddmm_kernel_count": (ctypes.c_longlong, [P]),
+        "lddmm_device_bytes": (ctypes.c_ulonglong, [P]),
         "lddmm_probe": (I, [P, ctypes.c_char_p]),
         "lddmm_probe_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(D)]),
@@ -123,7 +125,7 @@ class Context:
 
     def __init__(self, grid, K, alpha, s, sigma, Nt, precision="fp32", stream=None,
                  use_graphs=True, pcg_tol=1e-12, armijo_c=1e-4, max_halvings=10, persistent="auto",
-                 tensor_cores="auto"):
+                 tensor_cores="auto", recompute=False):
         L = lib()
         self.grid, self.K = tuple(int(g) for g in grid), tuple(int(k) for k in K)
         self.ndim = len(self.grid)
@@ -137,6 +139,7 @@ class Context:
         o.use_graphs = 1 if use_graphs else 0
         o.persistent = {True: 2, False: 0, "auto": 1}[persistent]
         o.tensor_cores = {True: 2, False: 0, "auto": 1}[tensor_cores]
+        o.recompute = 1 if recompute else 0
         o.pcg_tol, o.armijo_c, o.max_halvings = pcg_tol, armijo_c, max_halvings
         arr = ctypes.c_int * self.ndim
         h = ctypes.c_void_p()
@@ -269,3 +272,8 @@ class Context:
     @property
     def kernel_count(self):
         return int(lib().lddmm_kernel_count(self._h))
+
+    @property
+    def device_bytes(self):
+        """Device memory held by the context (all allocated at creation)."""
+        return int(lib().lddmm_device_bytes(self._h))

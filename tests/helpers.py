@@ -49,3 +49,37 @@ def problem(kind, Ns, Ks, seed, Nt, precision, max_disp=2.0, v_disp=2.0, **ctx_k
     ctx.set_images(torch_dev(I0, precision), torch_dev(I1, precision))
     P = objective.Problem(I0, I1, Ks, ALPHA, S, SIGMA, Nt)
     return ctx, P, v0, p
+
+
+# ---- central differences of the FP64 oracle's energy, one direction per task.
+# Runs in worker processes (spawn context): each worker builds the problem once.
+_FD_PROBLEM = {}
+
+
+def _fd_problem(name):
+    from oracle import objective
+    from paper_1807_11560_gb300 import inputs
+    if name not in _FD_PROBLEM:
+        kind, Ns, Ks, Nt, seed = inputs.WORKLOADS[name]
+        I0, I1 = inputs.make_pair(kind, Ns, seed)
+        I0, I1 = quantise(I0, "fp32"), quantise(I1, "fp32")
+        v0 = quantise(inputs.random_bl(Ks, 3, seed + 1, 2.0, Ns), "fp32")
+        _FD_PROBLEM[name] = (objective.Problem(I0, I1, Ks, ALPHA, S, SIGMA, Nt), v0, Ns, Ks)
+    return _FD_PROBLEM[name]
+
+
+def fd_data_term(task):
+    """(seed, directional derivative of the data term along the seeded direction,
+    the direction) by central differences of the oracle forward."""
+    from paper_1807_11560_gb300 import inputs
+    name, seed, eps = task
+    P, v0, Ns, Ks = _fd_problem(name)
+    p = inputs.random_bl(Ks, 3, seed, 1.0, Ns)
+    Ep = P.data_term(P.forward(v0 + eps * p)[3][-1])
+    Em = P.data_term(P.forward(v0 - eps * p)[3][-1])
+    return seed, (Ep - Em) / (2 * eps), p
+
+
+def spawn_pool(n):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(n)

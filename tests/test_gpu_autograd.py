@@ -10,7 +10,8 @@ from oracle import bl, objective, sweeps
 from paper_1807_11560_gb300 import Context, inputs
 from paper_1807_11560_gb300.autograd import shoot_transport
 
-from helpers import ALPHA, S, SIGMA, host, quantise, rel_2, torch_dev
+from helpers import (ALPHA, S, SIGMA, _fd_problem, fd_data_term, host, quantise, rel_2, spawn_pool,
+                     torch_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -64,33 +65,51 @@ def test_autograd_of_the_data_term_is_the_library_gradient():
 
 def test_differentiation_check_96cubed():
     """The 96^3 brain configuration, band 24^3, Nt = 16: GPU FP32 autograd against the
-    FP64 oracle's adjoint gradient (1e-5) and central differences of the FP64 oracle
-    forward (step 1e-3; the gap is the discretisation gap of the paper-form gradient)."""
+    FP64 oracle's adjoint gradient (1e-5) and against central differences of the FP64
+    oracle forward along 20 seeded directions (step 1e-3), with the image-grid
+    histories kept and regenerated (recompute mode); the device footprint of both
+    modes is printed.  The FD comparison measures the discretisation gap of the
+    paper-form gradient (it is not the exact derivative of the discrete energy away
+    from v0 = 0): the gradient must track the differences across directions."""
+    import os
     import torch
-    kind, Ns, Ks, Nt, seed = inputs.WORKLOADS["3d_96_brain"]
-    I0, I1 = inputs.make_pair(kind, Ns, seed)
-    I0, I1 = quantise(I0, "fp32"), quantise(I1, "fp32")
-    v0 = quantise(inputs.random_bl(Ks, 3, seed + 1, 2.0, Ns), "fp32")
-    free0 = torch.cuda.mem_get_info()[0]
-    ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision="fp32")
-    footprint = free0 - torch.cuda.mem_get_info()[0]
-    ctx.set_images(torch_dev(I0, "fp32"), torch_dev(I1, "fp32"))
-    v = torch_dev(v0, "fp32").requires_grad_(True)
-    m1 = shoot_transport(ctx, v)
-    I1d = torch_dev(I1, "fp32")
-    (((m1 - I1d) ** 2).mean() / SIGMA ** 2).backward()
-    g = host(v.grad)
-    P = objective.Problem(I0, I1, Ks, ALPHA, S, SIGMA, Nt)
-    lin = P.gradient(v0)
-    g_ref = P.L * (lin.g - v0)                               # l2 form of the data part
+    name = "3d_96_brain"
+    kind, Ns, Ks, Nt, seed = inputs.WORKLOADS[name]
+    seeds = list(range(2000, 2020))
+    pool = spawn_pool(min(len(seeds), os.cpu_count() or 1))   # before any oracle work here
+    try:
+        fd_async = pool.map_async(fd_data_term, [(name, s_, 1e-3) for s_ in seeds])
+        P, v0, _, _ = _fd_problem(name)
+        I0, I1 = P.I0.astype(np.float32), P.I1.astype(np.float32)
+        grads, footprint = {}, {}
+        for recompute in (False, True):
+            free0 = torch.cuda.mem_get_info()[0]
+            ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision="fp32", recompute=recompute)
+            footprint[recompute] = (ctx.device_bytes, free0 - torch.cuda.mem_get_info()[0])
+            ctx.set_images(torch_dev(I0, "fp32"), torch_dev(I1, "fp32"))
+            v = torch_dev(v0, "fp32").requires_grad_(True)
+            m1 = shoot_transport(ctx, v)
+            I1d = torch_dev(I1, "fp32")
+            (((m1 - I1d) ** 2).mean() / SIGMA ** 2).backward()
+            grads[recompute] = host(v.grad)
+            ctx.close()
+        lin = P.gradient(v0)
+        g_ref = P.L * (lin.g - v0)                           # l2 form of the data part
+        out = fd_async.get(timeout=3600)
+    finally:
+        pool.terminate()
+        pool.join()
+    g = grads[False]
     assert rel_2(g, g_ref) < 1e-5
-    gaps = []
-    for s in range(2000, 2003):
-        p = inputs.random_bl(Ks, 3, s, 1.0, Ns)
-        eps = 1e-3
-        Ep = P.data_term(P.forward(v0 + eps * p)[3][-1])
-        Em = P.data_term(P.forward(v0 - eps * p)[3][-1])
-        fd = (Ep - Em) / (2 * eps)
-        gaps.append(abs(fd - bl.inner_l2(g, p)) / abs(fd))
-    print(f"96^3: context footprint {footprint / 2**20:.0f} MiB; FD gaps {gaps}")
-    assert max(gaps) < 0.2
+    assert rel_2(grads[True], g) < 1e-6
+    fd = np.array([r[1] for r in out])
+    gp = np.array([bl.inner_l2(g, r[2]) for r in out])
+    rms = float(np.sqrt(np.mean(fd ** 2)))
+    gaps = np.abs(fd - gp) / rms
+    corr = float(np.corrcoef(fd, gp)[0, 1])
+    mib = {k: (a / 2**20, b / 2**20) for k, (a, b) in footprint.items()}
+    print(f"96^3 Nt=16: context MiB (held, measured) kept {mib[False]}, recompute {mib[True]}; "
+          f"FD gap / rms(fd): median {np.median(gaps):.3f} max {gaps.max():.3f}; corr {corr:.4f}")
+    assert footprint[True][0] < footprint[False][0]
+    assert corr > 0.95
+    assert gaps.max() < 0.5

@@ -105,6 +105,33 @@ def test_persistent_sweeps_equal_per_evaluation_launches(precision):
     np.testing.assert_array_equal(outs[0][2], outs[1][2])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_recompute_mode_equals_kept_histories(precision):
+    """Regenerating the image-grid histories in forward order (recompute mode) runs
+    the same kernels on the same inputs: energy, gradient, Hessian-vector product,
+    m(1) and the line-search energy must be bit-identical, with a smaller footprint."""
+    kind, Ns, Ks, seed, Nt = CASES[2]
+    outs, held = [], []
+    for recompute in (False, True):
+        ctx, P, v0, p = problem(kind, Ns, Ks, seed, Nt, precision, recompute=recompute)
+        held.append(ctx.device_bytes)
+        g = _cplx(precision, (3,) + Ks)
+        E = ctx.gradient(torch_dev(v0, precision), g)
+        Hp = _cplx(precision, (3,) + Ks)
+        ctx.hessvec(torch_dev(p, precision), Hp)
+        ctx.hessvec(torch_dev(p, precision), Hp)        # second call: graph replay
+        E2 = ctx.energy(torch_dev(v0 + 0.5 * p, precision))
+        Hp2 = _cplx(precision, (3,) + Ks)
+        ctx.hessvec(torch_dev(p, precision), Hp2)        # linearisation point kept across energy()
+        outs.append((E, host(g), host(Hp), E2, host(Hp2)))
+        ctx.close()
+    assert outs[0][0] == outs[1][0] and outs[0][3] == outs[1][3]
+    for k in (1, 2, 4):
+        np.testing.assert_array_equal(outs[0][k], outs[1][k])
+    np.testing.assert_array_equal(outs[0][2], outs[0][4])
+    assert held[1] < held[0]
+
+
 def test_host_pointers_and_state_errors():
     kind, Ns, Ks, seed, Nt = CASES[0]
     ctx, P, v0, p = problem(kind, Ns, Ks, seed, Nt, "fp32")
