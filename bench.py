@@ -405,10 +405,90 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_population(args):
+    """The batched population workload (32 brain pairs of uneven grids and bands):
+    one step = one GN iteration with 20 PCG Hessian-vector products on every pair,
+    all pairs at once through lddmm_batch_gn_solve (one CUDA stream and one host
+    thread per context).  The work spans 32 streams, so steps are timed by the host
+    clock between device synchronisations.  Also reported: the same contexts solved
+    one after another, and the population with plain FP32 SIMT transforms instead of
+    the tcgen05 3xTF32 split."""
+    import collections
+
+    import numpy as np
+    import torch
+
+    from paper_1807_11560_gb300 import Context, batch_gn_solve, inputs
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    pop = inputs.population()
+
+    def make(tc):
+        made = []
+        for kind, Ns, Ks, Nt, seed in pop:
+            I0, I1 = inputs.make_pair(kind, Ns, seed)
+            st = torch.cuda.Stream()
+            ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision="fp32", stream=st.cuda_stream,
+                          tensor_cores=tc, persistent=False)
+            I0d = torch.as_tensor(I0, dtype=torch.float32, device="cuda")
+            I1d = torch.as_tensor(I1, dtype=torch.float32, device="cuda")
+            torch.cuda.synchronize()
+            ctx.set_images(I0d, I1d)
+            made.append((ctx, st, np.zeros((3,) + tuple(Ks), np.complex64)))
+        return made
+
+    def timed(made, steps, threads):
+        ctxs = [m[0] for m in made]
+        hv, t = 0, 0.0
+        for _ in range(steps):
+            v0s = [np.zeros_like(m[2]) for m in made]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            reps = batch_gn_solve(ctxs, v0s, 1, N_PCG, threads=threads)
+            torch.cuda.synchronize()
+            t += time.perf_counter() - t0
+            hv += sum(r["pcg_iters"] for r in reps)
+        return hv / t, t / steps, v0s
+
+    made = make("auto")
+    timed(made, args.warmup, 0)
+    value, step_s, v_tc = timed(made, args.steps, 0)
+    seq_value, _, _ = timed(made, 1, 1)
+    held = sum(m[0].device_bytes for m in made)
+    for m in made:
+        m[0].close()
+    del made
+    made = make(False)
+    timed(made, 1, 0)
+    plain_value, _, v_plain = timed(made, args.steps, 0)
+    for m in made:
+        m[0].close()
+    # one GN step from v0 = 0 on the same images: the two precisions' updates
+    diffs = [float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)) for a, b in zip(v_tc, v_plain)]
+    hist = collections.Counter(f"{'x'.join(map(str, g))}/K{k[0]}" for _, g, k, _, _ in pop)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "population_32", "pairs": len(pop), "grids_bands": dict(hist), "Nt": 10,
+                   "pcg_per_gn": N_PCG, "step": "one GN iteration on every pair",
+                   "timer": "host clock between device synchronisations (32 streams)",
+                   "tensor_cores": "auto (grids of at least 2^20 voxels)"},
+        "sequential_value": seq_value,
+        "plain_fp32_value": plain_value,
+        "split_vs_plain_rel_update_diff_max": max(diffs),
+        "device_bytes_held": held,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "population_32":
+        run_population(args)
     else:
         run_gpu(args)
 

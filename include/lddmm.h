@@ -168,6 +168,20 @@ int lddmm_hessvec(lddmm_ctx* ctx, const void* dv, void* Hdv_out);
  * accepts no step. */
 int lddmm_gn_solve(lddmm_ctx* ctx, void* v0_inout, int n_gn, int n_pcg, lddmm_report* rep);
 
+/* Batched population: lddmm_gn_solve on n independent contexts at once (one
+ * registration per context: its own grid, band, images and v0s[i]), driven
+ * from min(n, nthreads) host threads (0: one per hardware thread).  Each
+ * context runs its calls in order on its own opts.stream, so contexts created
+ * with distinct non-NULL streams overlap on the GPU; contexts sharing a stream
+ * (or the legacy NULL stream) serialise but stay correct.  Contexts whose
+ * sweeps would run as persistent cooperative kernels are refused
+ * (LDDMM_EINVAL): independent cooperative grids are not guaranteed to be
+ * co-resident.  reps: NULL or n reports.  Returns LDDMM_OK or the first
+ * failing context's status (its lddmm_last_error says why); every context is
+ * run to the end whatever the others return. */
+int lddmm_batch_gn_solve(lddmm_ctx* const* ctxs, int n, void* const* v0s, int n_gn, int n_pcg,
+                         lddmm_report* reps, int nthreads);
+
 /* ---------------------------------------------------------------------------
  * Component calls: single steps of the hot path, exposed for testing and for
  * callers composing their own solvers.  Same conventions as above.

@@ -6,5 +6,5 @@ sm_103a, built by ``paper_1807_11560_gb300.build``); ``Context`` is its thin
 Python binding and ``inputs`` holds the seeded synthetic phantoms.
 """
 
-from .lddmm import Context, LddmmError, lib  # noqa: F401
+from .lddmm import Context, LddmmError, batch_gn_solve, lib  # noqa: F401
 from . import inputs  # noqa: F401

@@ -14,6 +14,7 @@
 // Hessian-vector product can be captured once per linearisation point into a
 // CUDA graph and replayed.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <initializer_list>
 #include <utility>
@@ -21,6 +22,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/lddmm.h"
@@ -1194,6 +1196,48 @@ int lddmm_gn_solve(lddmm_ctx* ctx, void* v0, int n_gn, int n_pcg, lddmm_report* 
     return LDDMM_EINVAL;
   }
   return lddmm::dispatch(ctx, [&](auto& im) { im.gn_solve(v0, n_gn, n_pcg, rep); });
+}
+
+int lddmm_batch_gn_solve(lddmm_ctx* const* ctxs, int n, void* const* v0s, int n_gn, int n_pcg,
+                         lddmm_report* reps, int nthreads) {
+  if (!ctxs || !v0s || n < 1 || n_gn < 0 || n_pcg < 1 || nthreads < 0) return LDDMM_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || !ctxs[i]->impl) return LDDMM_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) {
+        ctxs[i]->err = "a context appears twice in the batch";
+        return LDDMM_EINVAL;
+      }
+    if (bad_ptr(ctxs[i], v0s[i], "v0_inout")) return LDDMM_EINVAL;
+    // independent cooperative grids are not guaranteed to be co-resident, so
+    // contexts whose sweeps would run as persistent kernels cannot share the GPU
+    const bool pers = ctxs[i]->precision == LDDMM_FP64
+                          ? static_cast<Impl<double>*>(ctxs[i]->impl)->persistent()
+                          : static_cast<Impl<float>*>(ctxs[i]->impl)->persistent();
+    if (pers) {
+      ctxs[i]->err = "batched contexts need opts.persistent = 0 (or padded grids above 32^3)";
+      return LDDMM_EINVAL;
+    }
+  }
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nw = std::min(n, nthreads > 0 ? nthreads : (int)hw);
+  std::vector<int> status(n, LDDMM_OK);
+  std::atomic<int> next{0};
+  auto work = [&] {
+    for (int i = next++; i < n; i = next++)
+      status[i] = lddmm_gn_solve(ctxs[i], v0s[i], n_gn, n_pcg, reps ? reps + i : nullptr);
+  };
+  std::vector<std::thread> pool;
+  try {
+    for (int w = 1; w < nw; ++w) pool.emplace_back(work);
+  } catch (...) {
+    // fewer threads than asked: the calling thread still drains the queue
+  }
+  work();
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < n; ++i)
+    if (status[i] != LDDMM_OK) return status[i];
+  return LDDMM_OK;
 }
 
 int lddmm_iota(lddmm_ctx* ctx, const void* a, int ncomp, void* f) {

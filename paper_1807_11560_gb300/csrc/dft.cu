@@ -34,11 +34,12 @@ using dev::kMaxSmem;
 
 template <auto Kernel>
 void allow_smem() {
-  static bool done = false;   // one attribute call per kernel instantiation
-  if (!done) {
+  // one attribute call per kernel instantiation (thread-safe static init)
+  static const bool done = [] {
     cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-    done = true;
-  }
+    return true;
+  }();
+  (void)done;
 }
 
 template <typename T, bool TWS>

@@ -191,6 +191,22 @@ WORKLOADS = {
 }
 
 
+def population(n=32, seed=3000):
+    """The batched population-to-atlas workload: n brain-phantom pairs, pair i with
+    a grid drawn uniformly from {96^3, 128^3, 160x192x160} and a band from
+    {24^3, 32^3} (both draws from `seed`), pair seed seed + 1 + i, Nt = 10.
+    Entries have the WORKLOADS layout (kind, grid, band, Nt, seed)."""
+    rng = np.random.default_rng(seed)
+    grids = [(96, 96, 96), (128, 128, 128), (160, 192, 160)]
+    bands = [(24, 24, 24), (32, 32, 32)]
+    out = []
+    for i in range(n):
+        g = grids[int(rng.integers(len(grids)))]
+        k = bands[int(rng.integers(len(bands)))]
+        out.append(("brain", g, k, 10, seed + 1 + i))
+    return out
+
+
 def make_pair(kind, Ns, seed, max_disp=3.0):
     """(I0, I1): a phantom and its analytically warped copy."""
     Ns = tuple(int(n) for n in Ns)

@@ -44,6 +44,50 @@ class Report(ctypes.Structure):
                 ("pcg_hist", ctypes.POINTER(ctypes.c_int))]
 
 
+def _report(n_gn):
+    """A Report with caller-owned history arrays (kept alive by the second item)."""
+    r = Report()
+    E = (ctypes.c_double * max(1, n_gn))()
+    eps = (ctypes.c_double * max(1, n_gn))()
+    its = (ctypes.c_int * max(1, n_gn))()
+    r.E_hist = ctypes.cast(E, ctypes.POINTER(ctypes.c_double))
+    r.eps_hist = ctypes.cast(eps, ctypes.POINTER(ctypes.c_double))
+    r.pcg_hist = ctypes.cast(its, ctypes.POINTER(ctypes.c_int))
+    return r, (E, eps, its)
+
+
+def _report_dict(r, keep):
+    E, eps, its = keep
+    n = r.gn_iters
+    extra = 1 if r.ls_failed else 0
+    return {"gn_iters": n, "pcg_iters": r.pcg_iters, "ls_failed": bool(r.ls_failed),
+            "E_initial": r.E_initial, "E_final": r.E_final, "gnorm_initial": r.gnorm_initial,
+            "gnorm_final": r.gnorm_final, "E": list(E[:n + extra][:max(n, 1)]),
+            "eps": list(eps[:n]), "pcg": list(its[:n + extra])}
+
+
+def batch_gn_solve(contexts, v0s, n_gn, n_pcg, threads=0):
+    """lddmm_batch_gn_solve: GN-Krylov on independent registrations at once (each
+    Context on its own stream); v0s are updated in place.  Returns the reports."""
+    n = len(contexts)
+    if n != len(v0s) or n == 0:
+        raise ValueError("one v0 per context")
+    hs = (ctypes.c_void_p * n)(*[c._h for c in contexts])
+    ps = (ctypes.c_void_p * n)(*[c._arg(v, "cplx", c.nband) for c, v in zip(contexts, v0s)])
+    reps = (Report * n)()
+    keeps = []
+    for i in range(n):
+        r, keep = _report(n_gn)
+        reps[i] = r
+        keeps.append(keep)
+    code = lib().lddmm_batch_gn_solve(hs, n, ps, int(n_gn), int(n_pcg), reps, int(threads))
+    if code != 0:
+        bad = [c for c in contexts if lib().lddmm_last_error(c._h)]
+        msg = "; ".join(lib().lddmm_last_error(c._h).decode() for c in bad) or "batch failed"
+        raise LddmmError(code, msg)
+    return [_report_dict(reps[i], keeps[i]) for i in range(n)]
+
+
 def lib():
     """Load liblddmm.so (raises if it has not been built)."""
     global _lib
@@ -63,6 +107,8 @@ def lib():
         "lddmm_gradient": (I, [P, P, P, ctypes.POINTER(D)]),
         "lddmm_hessvec": (I, [P, P, P]),
         "lddmm_gn_solve": (I, [P, P, I, I, ctypes.POINTER(Report)]),
+        "lddmm_batch_gn_solve": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P), I, I,
+                                     ctypes.POINTER(Report), I]),
         "lddmm_iota": (I, [P, P, I, P]),
         "lddmm_pi": (I, [P, P, I, P]),
         "lddmm_ad_dagger": (I, [P, P, P, P]),
@@ -209,20 +255,10 @@ class Context:
                                         self._arg(out, "cplx", self.nband)))
 
     def gn_solve(self, v0_inout, n_gn, n_pcg):
-        r = Report()
-        E = (ctypes.c_double * max(1, n_gn))()
-        eps = (ctypes.c_double * max(1, n_gn))()
-        its = (ctypes.c_int * max(1, n_gn))()
-        r.E_hist = ctypes.cast(E, ctypes.POINTER(ctypes.c_double))
-        r.eps_hist = ctypes.cast(eps, ctypes.POINTER(ctypes.c_double))
-        r.pcg_hist = ctypes.cast(its, ctypes.POINTER(ctypes.c_int))
+        r, keep = _report(n_gn)
         self._check(lib().lddmm_gn_solve(self._h, self._arg(v0_inout, "cplx", self.nband), int(n_gn),
                                          int(n_pcg), ctypes.byref(r)))
-        n = r.gn_iters
-        return {"gn_iters": n, "pcg_iters": r.pcg_iters, "ls_failed": bool(r.ls_failed),
-                "E_initial": r.E_initial, "E_final": r.E_final, "gnorm_initial": r.gnorm_initial,
-                "gnorm_final": r.gnorm_final, "E": list(E[:n + (1 if r.ls_failed else 0)][:max(n, 1)]),
-                "eps": list(eps[:n]), "pcg": list(its[:n + (1 if r.ls_failed else 0)])}
+        return _report_dict(r, keep)
 
     def iota(self, a, ncomp, out):
         kv, nv = int(np.prod(self.K)), self.nvox
