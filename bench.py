@@ -387,7 +387,8 @@ def run_gpu(args):
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{world}",
                        "tensor_cores": f"{args.tensor_cores} (tcgen05 3xTF32 image-grid iota; "
-                                       "auto = grids of at least 2^20 voxels)"},
+                                       "auto = grids of at least 2^20 voxels)",
+                       "tiles": dict(zip(("iota_ab_twiddles", "cpw_pencils", "pi_rows"), ctx.tiles))},
             "gn_solve_s": 1e-3 * statistics.mean(step_ms) * N_GN_CONFIG,
             "gn_solve_note": f"{N_GN_CONFIG} GN x {N_PCG} PCG at the mean timed step time",
             "hessvec_per_s_fixed_point": hv_fixed,

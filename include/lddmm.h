@@ -100,6 +100,12 @@ typedef struct {
                            floats per voxel (plus the transform scratch), and each
                            Hessian-vector product re-runs the state transport (Nt steps
                            and 2 (Nt + 1) vector iotas more). */
+  int autotune;         /* 1 (default): at creation, time the candidate tile shapes of the
+                           three padded-grid bracket kernels (twiddle staging, pencils per
+                           tile, band rows per item) on this context's sizes and keep the
+                           fastest; 0: size heuristics.  Contexts whose sweeps run as
+                           persistent kernels keep the heuristics.  No result depends on
+                           the tile shapes. */
 } lddmm_opts;
 
 /* Report of lddmm_gn_solve.  The per-iteration arrays are optional
@@ -119,7 +125,8 @@ typedef struct {
 
 /* Defaults for lddmm_opts (precision FP32, legacy stream, tol 1e-12,
  * c = 1e-4, 10 halvings, graphs on, persistent sweeps on small grids,
- * tensor-core image-grid transforms on large grids). */
+ * tensor-core image-grid transforms on large grids, kept histories,
+ * autotuned tiles). */
 void lddmm_default_opts(lddmm_opts* opts);
 
 /* Create a registration context (Section 3.2).
@@ -280,6 +287,12 @@ int lddmm_probe_read(lddmm_ctx* ctx, double* total_ms, long long* launches, doub
 /* Number of CUDA kernels this context has launched since creation (graph
  * replays count each kernel node). */
 long long lddmm_kernel_count(const lddmm_ctx* ctx);
+
+/* Tile shapes the context's padded-grid bracket kernels use (after the
+ * autotuner, or the size heuristics): tws 1/2 = iota A+B twiddles from global
+ * / shared memory, tp = pencils per C/products/C' tile, kc = band rows per
+ * pi B'/A' item.  LDDMM_EINVAL on NULL arguments. */
+int lddmm_tile_config(const lddmm_ctx* ctx, int* tws, int* tp, int* kc);
 
 /* Bytes of device memory the context holds (all of it is allocated by
  * lddmm_create; no later call allocates).  0 for NULL. */

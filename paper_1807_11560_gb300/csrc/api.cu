@@ -202,6 +202,91 @@ struct Impl {
     alloc(S.mh, steps * Nvol);
     alloc(S.off, (opts.recompute ? 1 : (size_t)Nt) * 3 * Nvol);
   }
+  // ------------------------------------------------------------ autotuner
+  // Times the candidate tile shapes of the three padded-grid bracket kernels
+  // on this context's sizes (CUDA events on the context stream, best of three
+  // after a warm-up launch) and keeps the fastest of each.  Tile shapes change
+  // no result: every sum keeps its order whatever the tiling.
+  void autotune() {
+    const size_t bbytes = (size_t)3 * Kvol * sizeof(C);
+    cuda(cudaMemsetAsync(px, 0, bbytes, st), "memset");
+    cuda(cudaMemsetAsync(pr, 0, bbytes, st), "memset");
+    static const int kTp[] = {1, 2, 4, 8, 16};
+    static const int kKc[] = {1, 2, 3, 4, 6, 8};
+    long long slot_max = 0;
+    for (int tp : kTp) {
+      if (!tile_valid<T>(pad, 0, tp, 0)) continue;
+      Plan<T> q = pad;
+      q.tp = tp;
+      slot_max = std::max(slot_max, cache_slot_elems<T>(q));
+    }
+    T* slot = nullptr;
+    cuda(cudaMalloc(&slot, (size_t)std::max(1LL, slot_max) * sizeof(T)), "autotune scratch");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    try {
+      cuda(cudaMemsetAsync(slot, 0, (size_t)std::max(1LL, slot_max) * sizeof(T), st), "memset");
+      cuda(cudaEventCreate(&e0), "event");
+      cuda(cudaEventCreate(&e1), "event");
+      auto best_of = [&](auto&& launch) {
+        launch();
+        check_launch("autotune");
+        float best = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+          cuda(cudaEventRecord(e0, st), "event");
+          launch();
+          cuda(cudaEventRecord(e1, st), "event");
+          cuda(cudaEventSynchronize(e1), "autotune");
+          float ms = 0.f;
+          cuda(cudaEventElapsedTime(&ms, e0, e1), "event");
+          best = std::min(best, ms);
+        }
+        return best;
+      };
+      const IotaDesc<T> d = block24(px, pr, slot);
+      float best = 1e30f;
+      int pick = 0;
+      for (int tws : {1, 2}) {
+        if (!tile_valid<T>(pad, tws, 0, 0)) continue;
+        pad.tws = tws;
+        const float t = best_of([&] { bracket_iota<T>(pad, d, Lhat, T2, st); });
+        if (t < best) { best = t; pick = tws; }
+      }
+      pad.tws = pick;
+      best = 1e30f;
+      pick = 0;
+      for (int tp : kTp) {
+        if (!tile_valid<T>(pad, pad.tws, tp, 0)) continue;
+        pad.tp = tp;
+        const float t = best_of([&] { bracket_cpw<T>(pad, PW_GT, T2, slot, P2, st); });
+        if (t < best) { best = t; pick = tp; }
+      }
+      pad.tp = pick;
+      PiEpi<T> e = epi(3, 3);
+      for (int o = 0; o < 3; ++o) {
+        e.grp[o] = 0;
+        e.coef[o] = (T)1;
+      }
+      add_out(e, vout, 0, 1.0, {});
+      best = 1e30f;
+      pick = 0;
+      for (int kc : kKc) {
+        if (!tile_valid<T>(pad, pad.tws, pad.tp, kc)) continue;
+        pad.kc = kc;
+        const float t = best_of([&] { bracket_pi<T>(pad, e, Lhat, P2, st); });
+        if (t < best) { best = t; pick = kc; }
+      }
+      pad.kc = pick;
+    } catch (...) {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      cudaFree(slot);
+      throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(slot);
+  }
+
   // image-grid history accessors (step n of a kept or a two-step rolling history)
   long long hstep(int n) const { return opts.recompute ? (n & 1) : n; }
   T* mstate(State<T>& S, int n) { return S.mh + hstep(n) * Nvol; }
@@ -253,8 +338,6 @@ struct Impl {
 
     alloc(I0, (size_t)Nvol);
     alloc(I1, (size_t)Nvol);
-    make_state(lin);
-    make_state(trial);
     const long long H1 = K.h1;
     const long long t2 = std::max(33LL * H1 * N.n2 * N.n3, 24LL * H1 * M.n2 * M.n3);
     alloc(T2, (size_t)t2);
@@ -273,6 +356,9 @@ struct Impl {
     alloc(dres, 8);
     cuda(cudaMemset(dres, 0, 8 * sizeof(double)), "memset");
     cuda(cudaMallocHost(&hres, 8 * sizeof(double)), "cudaMallocHost");
+    if (opts.autotune && !persistent()) autotune();
+    make_state(lin);                       // the cache layout follows the tile shapes
+    make_state(trial);
     alloc(bar, kSweepBarWords);
     record_sweeps();
     cuda(cudaDeviceSynchronize(), "create");
@@ -1116,6 +1202,7 @@ void lddmm_default_opts(lddmm_opts* o) {
   o->persistent = 1;
   o->tensor_cores = 1;
   o->recompute = 0;
+  o->autotune = 1;
 }
 
 int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, double alpha, int s,
@@ -1322,6 +1409,15 @@ long long lddmm_kernel_count(const lddmm_ctx* ctx) {
   if (!ctx || !ctx->impl) return 0;
   if (ctx->precision == LDDMM_FP64) return static_cast<const Impl<double>*>(ctx->impl)->launches;
   return static_cast<const Impl<float>*>(ctx->impl)->launches;
+}
+
+int lddmm_tile_config(const lddmm_ctx* ctx, int* tws, int* tp, int* kc) {
+  if (!ctx || !ctx->impl || !tws || !tp || !kc) return LDDMM_EINVAL;
+  if (ctx->precision == LDDMM_FP64)
+    lddmm::tile_config<double>(static_cast<const Impl<double>*>(ctx->impl)->pad, tws, tp, kc);
+  else
+    lddmm::tile_config<float>(static_cast<const Impl<float>*>(ctx->impl)->pad, tws, tp, kc);
+  return LDDMM_OK;
 }
 
 unsigned long long lddmm_device_bytes(const lddmm_ctx* ctx) {

@@ -592,6 +592,8 @@ __host__ __device__ inline size_t ab_smem(const Plan<T>& p, bool tws) {
 // per SM (large image-grid planes are latency-bound at one CTA per SM)
 template <typename T>
 __host__ __device__ inline bool ab_tws(const Plan<T>& p) {
+  if (p.tws == 1) return false;
+  if (p.tws == 2 && ab_smem(p, true) <= (size_t)kMaxSmem) return true;
   return ab_smem(p, true) <= (size_t)64 * 1024;
 }
 
@@ -603,7 +605,13 @@ __host__ __device__ inline size_t cpw_smem(const Plan<T>& p, int TP, int NP) {
 }
 
 template <typename T>
+inline bool cpw_tile_ok(const Plan<T>& p, int TP) {
+  return TP >= 1 && cpw_smem(p, TP, 9) <= (size_t)kMaxSmem && p.g.n1 * TP <= 2 * kThreads;
+}
+
+template <typename T>
 inline int cpw_tile(const Plan<T>& p) {
+  if (p.tp > 0 && cpw_tile_ok(p, p.tp)) return p.tp;
   const long long P = (long long)p.g.n2 * p.g.n3;
   int TP = (int)std::max(1LL, std::min(8LL, P / 152));
   // products: at most two points per thread, and the tile must fit shared memory
@@ -625,7 +633,7 @@ inline BAGeom ba_geom(const Plan<T>& p, int ncomp, int nper) {
   const int G2 = p.g.n2, G3 = p.g.n3, K2 = p.b.k2;
   const int groups = ncomp * p.b.h1;
   const int want = std::max(1, (304 + groups - 1) / groups);
-  int KC = std::max(1, (K2 + want - 1) / want);
+  int KC = p.kc > 0 ? p.kc : std::max(1, (K2 + want - 1) / want);
   KC = std::min(std::min(KC, kMaxKC), K2);
   const int ncol = nper * G3;
   const int R = std::max(1, std::min(kMaxRows, kThreads / ncol));

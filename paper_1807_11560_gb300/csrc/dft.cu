@@ -181,6 +181,25 @@ size_t max_smem_needed(const Plan<T>& p, int nper_max, bool brackets) {
 size_t smem_limit() { return kMaxSmem; }
 
 template <typename T>
+void tile_config(const Plan<T>& p, int* tws, int* tp, int* kc) {
+  *tws = dev::ab_tws(p) ? 2 : 1;
+  *tp = dev::cpw_tile(p);
+  *kc = dev::ba_geom(p, 3, 3).KC;
+}
+
+template <typename T>
+bool tile_valid(const Plan<T>& p, int tws, int tp, int kc) {
+  if (tws == 2 && dev::ab_smem(p, true) > (size_t)kMaxSmem) return false;
+  if (tp > 0 && !dev::cpw_tile_ok(p, tp)) return false;
+  if (kc > p.b.k2 || kc > dev::kMaxKC) return false;
+  Plan<T> q = p;
+  q.tws = tws;
+  q.tp = tp;
+  q.kc = kc;
+  return max_smem_needed(q, 3, true) <= (size_t)kMaxSmem;
+}
+
+template <typename T>
 long long cache_slot_elems(const Plan<T>& p) {
   const long long P = (long long)p.g.n2 * p.g.n3;
   const int TP = dev::cpw_tile(p);
@@ -272,6 +291,8 @@ void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T
 #define LDDMM_DFT_INST(T)                                                                          \
   template size_t max_smem_needed<T>(const Plan<T>&, int, bool);                                   \
   template long long cache_slot_elems<T>(const Plan<T>&);                                           \
+  template void tile_config<T>(const Plan<T>&, int*, int*, int*);                                   \
+  template bool tile_valid<T>(const Plan<T>&, int, int, int);                                        \
   template void iota_batch<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t,    \
                               double*);                                                            \
   template void pi_batch<T>(const Plan<T>&, const PiSrc<T>&, const PiEpi<T>&, const T*, cplx<T>*,  \

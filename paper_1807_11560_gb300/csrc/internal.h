@@ -47,6 +47,11 @@ struct Plan {
   cplx<T>* E1b;
   cplx<T>* E2b;
   cplx<T>* E3b;
+  // tile overrides of the bracket kernels, set by the autotuner (0: the size
+  // heuristics): tws 1 = twiddles from global memory, 2 = staged in shared
+  // memory (iota A+B); tp = pencils per tile (C/products/C'); kc = band rows
+  // per item (pi B'/A')
+  int tws = 0, tp = 0, kc = 0;
 };
 
 // iota batch: field f is iota of (multiplier x one scalar band slab), where
@@ -160,6 +165,14 @@ size_t smem_limit();
 // [tile][24][M1][TP] so that a tile's fields are one contiguous block
 template <typename T>
 long long cache_slot_elems(const Plan<T>& p);
+// tile shapes in effect for a padded-grid plan (overrides or size heuristics):
+// twiddle staging of iota A+B (1 off, 2 on), pencils per tile of the
+// C/products/C' phase, band rows per pi B'/A' item (for 3 product fields)
+template <typename T>
+void tile_config(const Plan<T>& p, int* tws, int* tp, int* kc);
+// whether a tile override is usable on this plan
+template <typename T>
+bool tile_valid(const Plan<T>& p, int tws, int tp, int kc);
 
 // ---- grid kernels (grid.cu) -----------------------------------------------
 // Semi-Lagrangian state step (Eq. 52): m_next(x) = m(X_n(x)), foot point from

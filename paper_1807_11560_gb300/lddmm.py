@@ -32,7 +32,7 @@ class Opts(ctypes.Structure):
                 ("pcg_tol", ctypes.c_double), ("armijo_c", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("persistent", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("recompute", ctypes.c_int)]
+                ("recompute", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -119,6 +119,7 @@ def lib():
         "lddmm_transport_vjp": (I, [P, P, P, P]),
         "lddmm_kernel_count": (ctypes.c_longlong, [P]),
         "lddmm_device_bytes": (ctypes.c_ulonglong, [P]),
+        "lddmm_tile_config": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "lddmm_probe": (I, [P, ctypes.c_char_p]),
         "lddmm_probe_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(D)]),
@@ -171,7 +172,7 @@ class Context:
 
     def __init__(self, grid, K, alpha, s, sigma, Nt, precision="fp32", stream=None,
                  use_graphs=True, pcg_tol=1e-12, armijo_c=1e-4, max_halvings=10, persistent="auto",
-                 tensor_cores="auto", recompute=False):
+                 tensor_cores="auto", recompute=False, autotune=True):
         L = lib()
         self.grid, self.K = tuple(int(g) for g in grid), tuple(int(k) for k in K)
         self.ndim = len(self.grid)
@@ -186,6 +187,7 @@ class Context:
         o.persistent = {True: 2, False: 0, "auto": 1}[persistent]
         o.tensor_cores = {True: 2, False: 0, "auto": 1}[tensor_cores]
         o.recompute = 1 if recompute else 0
+        o.autotune = 1 if autotune else 0
         o.pcg_tol, o.armijo_c, o.max_halvings = pcg_tol, armijo_c, max_halvings
         arr = ctypes.c_int * self.ndim
         h = ctypes.c_void_p()
@@ -308,6 +310,13 @@ class Context:
     @property
     def kernel_count(self):
         return int(lib().lddmm_kernel_count(self._h))
+
+    @property
+    def tiles(self):
+        """(twiddle staging 1/2, pencils per tile, band rows per item) in effect."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(lib().lddmm_tile_config(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
 
     @property
     def device_bytes(self):

@@ -132,6 +132,25 @@ def test_recompute_mode_equals_kept_histories(precision):
     assert held[1] < held[0]
 
 
+def test_autotuned_tiles_change_no_result():
+    """The autotuner only picks tile shapes (twiddle staging, pencils per tile, band
+    rows per item); every sum keeps its order, so results are bit-identical."""
+    kind, Ns, Ks, seed, Nt = "ellipsoids", (40, 36, 34), (12, 10, 8), 41, 3
+    outs = []
+    for autotune in (False, True):
+        ctx, P, v0, p = problem(kind, Ns, Ks, seed, Nt, "fp32", persistent=False, autotune=autotune)
+        g = _cplx("fp32", (3,) + Ks)
+        E = ctx.gradient(torch_dev(v0, "fp32"), g)
+        Hp = _cplx("fp32", (3,) + Ks)
+        ctx.hessvec(torch_dev(p, "fp32"), Hp)
+        outs.append((E, host(g), host(Hp), ctx.tiles))
+        ctx.close()
+    print("tiles heuristic", outs[0][3], "autotuned", outs[1][3])
+    assert outs[0][0] == outs[1][0]
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    np.testing.assert_array_equal(outs[0][2], outs[1][2])
+
+
 def test_host_pointers_and_state_errors():
     kind, Ns, Ks, seed, Nt = CASES[0]
     ctx, P, v0, p = problem(kind, Ns, Ks, seed, Nt, "fp32")
