@@ -396,6 +396,15 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
 constexpr int kMaxKC = 8;
 constexpr int kMaxRows = 8;   // row groups R of B'
 constexpr int kEpiX = kMaxOut * kMaxX;
+
+// row stride of the transposed E3 twiddles in phase_pi_ba: an odd multiple of
+// half a 128-byte bank line, so the kRed-lane groups of different band slots
+// of a warp read different banks
+template <typename T>
+__host__ __device__ __forceinline__ int e3_stride(int G3) {
+  constexpr int E = 128 / (int)sizeof(cplx<T>);
+  return G3 + ((E / 2 - G3 % E) + E) % E;
+}
 struct BAGeom {
   int KC, nch, XB, R;
 };
@@ -413,10 +422,12 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
   const int ncol = nper * G3;
   C* slab = reinterpret_cast<C*>(smraw);                   // [nper][XB][G3]
   C* E2s = slab + nper * XB * G3;                          // [G2][KC]
-  C* E3s = E2s + G2 * KC;                                  // [K3][G3] (transposed E3b)
-  C* S1 = E3s + G3 * K3;                                   // [R][nper][KC][G3] (part 0: the sums)
-  C* sX = S1 + R * nper * KC * G3;                         // [KC K3][kEpiX] epilogue terms
-  T* sLh = reinterpret_cast<T*>(sX + KC * K3 * kEpiX);     // [KC K3] L^ of the band slots
+  const int G3s = e3_stride<T>(G3);
+  C* E3s = E2s + G2 * KC;                                  // [K3][G3s] (transposed E3b)
+  C* S1 = E3s + G3s * K3;                                  // [R][nper][KC][G3] (part 0: the sums)
+  const int NS = KC * K3;                                  // band slots of an item (at most)
+  C* sX = S1 + R * nper * KC * G3;                         // [kEpiX][NS] epilogue terms
+  T* sLh = reinterpret_cast<T*>(sX + NS * kEpiX);          // [NS] L^ of the band slots
   const int chunk = vb % nch;
   const int h = (vb / nch) % H1;
   const int c = vb / (nch * H1);
@@ -432,15 +443,15 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
   }
   for (int i = tid; i < G3 * K3; i += kThreads) {
     const int x = i / K3, k = i - x * K3;
-    cp_async(E3s + k * G3 + x, p.E3b + i);
+    cp_async(E3s + k * G3s + x, p.E3b + i);
   }
   for (int i = tid; i < nslot * kEpiX; i += kThreads) {
-    const int it = i / kEpiX, jq = i - it * kEpiX;
+    const int jq = i / nslot, it = i - jq * nslot;
     const int j = jq / kMaxX, q = jq - j * kMaxX;
     if (j < nout && q < e.nx[j]) {
       const int kk = it / K3, k3 = it - kk * K3;
       const long long at = (long long)c * kvol + ((long long)h * K2 + kb + kk) * K3 + k3;
-      cp_async(sX + i, e.X[j][q] + at);
+      cp_async(sX + jq * NS + it, e.X[j][q] + at);
     }
   }
   for (int it = tid; it < nslot; it += kThreads) {
@@ -520,7 +531,7 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
       C y = zero;
       if (live) {
         const C* row = S1 + (o * KC + kk) * G3;
-        const C* er = E3s + k3 * G3;
+        const C* er = E3s + k3 * G3s;
         for (int x = part; x < G3; x += kRed) cmac(y, row[x], er[x]);
       }
 #pragma unroll
@@ -558,11 +569,11 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
         v.x = e.cR[j] * Rj.x;
         v.y = e.cR[j] * Rj.y;
       }
-      const C* xs = sX + it * kEpiX + j * kMaxX;
+      const C* xs = sX + j * kMaxX * NS + it;
 #pragma unroll
       for (int q = 0; q < kMaxX; ++q) {
         if (q < e.nx[j]) {
-          const C x = xs[q];
+          const C x = xs[q * NS];
           v.x += e.cX[j][q] * x.x;
           v.y += e.cX[j][q] * x.y;
         }
@@ -623,7 +634,8 @@ inline int cpw_tile(const Plan<T>& p) {
 template <typename T>
 inline size_t ba_smem(const Plan<T>& p, int nper, const BAGeom& g) {
   const size_t G2 = p.g.n2, G3 = p.g.n3, K3 = p.b.k3, KC = g.KC;
-  return ((size_t)nper * g.XB * G3 + G2 * KC + G3 * K3 + (size_t)g.R * nper * KC * G3 + KC * K3 * kEpiX) *
+  const size_t G3s = (size_t)e3_stride<T>(p.g.n3);
+  return ((size_t)nper * g.XB * G3 + G2 * KC + G3s * K3 + (size_t)g.R * nper * KC * G3 + KC * K3 * kEpiX) *
              sizeof(cplx<T>) +
          KC * K3 * sizeof(T);
 }

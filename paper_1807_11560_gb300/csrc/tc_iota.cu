@@ -1,26 +1,29 @@
 // Tensor-core (tcgen05, sm_103a) form of the image-grid iota stage C, the
 // k1 -> x1 contraction of the band-limited-to-grid map (Eq. 46):
 //
-//   out_f[x1][i] = sum_h Re(E1f[h][x1] T2[f][h][i]) = sum_k A[x1][k] B_f[k][i]
-//   A[x1][2h] = Re E1f[h][x1],  A[x1][2h+1] = -Im E1f[h][x1]
-//   B_f[2h][i] = Re T2[f][h][i], B_f[2h+1][i] = Im T2[f][h][i]
+//   out_f[x1][i] = sum_h Re(E1f[h][x1] T2[f][h][i]) = sum_k A_f[i][k] B[x1][k]
+//   A_f[i][2h] = Re T2[f][h][i],  A_f[i][2h+1] = Im T2[f][h][i]
+//   B[x1][2h]  = Re E1f[h][x1],   B[x1][2h+1]  = -Im E1f[h][x1]
 //
-// a real GEMM with M = N1 (x1), K = K1 (padded to a multiple of 8) and
-// N = N2 N3 per field.  FP32 accuracy from TF32 tensor cores by the 3xTF32
-// split x = hi + lo (hi = TF32 rounding of x): A B ~ Ahi Bhi + Ahi Blo + Alo Bhi,
+// a real GEMM D = A B^T with M = 128 grid pencils i per tile, N = N1 (x1,
+// padded to a multiple of 16, at most 256) and K = K1 (padded to a multiple of
+// 8).  FP32 accuracy from TF32 tensor cores by the 3xTF32 split x = hi + lo
+// (hi = TF32 rounding of x): A B^T ~ Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T,
 // accumulated in FP32 in tensor memory.
 //
-// One CTA (256 threads) owns up to two 128-row M tiles (N1 <= 256) in 256
-// TMEM columns and walks (field, 128-column N tile) work items:
-//   1. all threads stage B (hi and lo) into shared memory in the K-major,
+// One CTA (256 threads) walks (field, 128-pencil tile) work items:
+//   1. all threads write the tile's T2 values (fetched into registers while
+//      the previous item ran) into shared memory, hi and lo, in the K-major
 //      no-swizzle canonical layout (8 x 16-byte core matrices);
-//   2. one thread issues the MMAs and commits them to an mbarrier;
-//   3. all threads wait (bounded), read their TMEM lane quadrant with
-//      tcgen05.ld and store rows of out.
-// A (the twiddles) is staged once per CTA.  D leaves TMEM in 32-column chunks
-// through a padded shared tile so that every warp stores 128 contiguous bytes.
-// At least 96 KB of shared memory keeps at most two CTAs on an SM, so the two
-// 256-column TMEM allocations always fit.
+//   2. one thread issues the MMAs into a TMEM accumulator (lane = pencil,
+//      column = x1) and commits them to an mbarrier; meanwhile every thread
+//      issues the global loads of its next item;
+//   3. all threads wait (bounded) and read their TMEM lane quadrant with
+//      tcgen05.ld: for each x1 a warp holds 32 consecutive pencils and stores
+//      them as one 128-byte row segment straight from registers.
+// B (the twiddles) is staged once per CTA.  At least 96 KB of shared memory
+// keeps at most two CTAs on an SM, so the two 256-column TMEM allocations
+// always fit.
 #include <algorithm>
 #include <cstdint>
 
@@ -30,11 +33,10 @@ namespace lddmm {
 namespace {
 
 constexpr int kThreadsTC = 256;
-constexpr int kNT = 128;                 // N tile (columns of D per M tile)
-constexpr int kMT = 128;                 // M tile (TMEM lanes)
+constexpr int kNT = 128;                 // grid pencils per work item
+constexpr int kMT = 128;                 // M tile (TMEM lanes = pencils)
 constexpr int kMaxKp = 48;               // K1 <= 48 (shared memory)
 constexpr long long kWaitLimit = 1LL << 24;
-constexpr int kStile = 128 * 33 + 4;     // padded D chunk, rounded to 16 bytes
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -97,16 +99,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 __global__ void __launch_bounds__(kThreadsTC)
-k_iota_C_tc(Plan<float> p, IotaDesc<float> d, const float2* __restrict__ T2, int Kp, int nmt, double* flag) {
+k_iota_C_tc(Plan<float> p, IotaDesc<float> d, const float2* __restrict__ T2, int Kp, int Np, double* flag) {
   extern __shared__ __align__(128) unsigned char smraw[];
   float* sm = reinterpret_cast<float*>(smraw);
-  const int tileA = kMT * Kp, tileB = kNT * Kp;
-  float* Ahi[2] = {sm, sm + 2 * tileA};
-  float* Alo[2] = {sm + tileA, sm + 3 * tileA};
-  float* Bhi = sm + 4 * tileA;
+  const int tileA = kMT * Kp, tileB = Np * Kp;
+  float* Ahi = sm;                                           // data tile (M = 128 pencils)
+  float* Alo = Ahi + tileA;
+  float* Bhi = Alo + tileA;                                  // twiddles (N = Np rows of x1)
   float* Blo = Bhi + tileB;
-  float* stile = Blo + tileB;                                // [128][33] D chunk for coalesced stores
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(stile + kStile);   // 16-byte aligned
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + tileB);  // 16-byte aligned (sizes are)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
   const int G1 = p.g.n1, H1 = p.b.h1, K = 2 * H1;
@@ -114,26 +115,25 @@ k_iota_C_tc(Plan<float> p, IotaDesc<float> d, const float2* __restrict__ T2, int
   const int ntn = (int)((P + kNT - 1) / kNT);
   const long long nitems = (long long)d.nf * ntn;
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int r = tid & (kNT - 1), h0 = tid >> 7;              // staging: pencil r, slots h0 + 2j
 
-  // A (both M tiles) and the zero K padding of B, once per CTA
-  for (int idx = tid; idx < 2 * kMT * Kp; idx += kThreadsTC) {
-    const int mt = idx / (kMT * Kp), rem = idx - mt * kMT * Kp;
-    const int r = rem / Kp, k = rem - r * Kp;
-    const int x1 = mt * kMT + r;
+  // B (both halves of the split) and the zero K padding of A, once per CTA
+  for (int idx = tid; idx < Np * Kp; idx += kThreadsTC) {
+    const int x1 = idx / Kp, k = idx - x1 * Kp;
     float v = 0.f;
     if (x1 < G1 && k < K) {
       const float2 e = p.E1f[(k >> 1) * G1 + x1];
       v = (k & 1) ? -e.y : e.x;
     }
     const float hi = tf32_hi(v);
-    const int o = kmajor_off(r, k, Kp);
-    Ahi[mt][o] = hi;
-    Alo[mt][o] = v - hi;
+    const int o = kmajor_off(x1, k, Kp);
+    Bhi[o] = hi;
+    Blo[o] = v - hi;
   }
-  for (int idx = tid; idx < kNT * (Kp - K); idx += kThreadsTC) {
-    const int r = idx / (Kp - K), k = K + idx % (Kp - K);
-    Bhi[kmajor_off(r, k, Kp)] = 0.f;
-    Blo[kmajor_off(r, k, Kp)] = 0.f;
+  for (int idx = tid; idx < kMT * (Kp - K); idx += kThreadsTC) {
+    const int row = idx / (Kp - K), k = K + idx % (Kp - K);
+    Ahi[kmajor_off(row, k, Kp)] = 0.f;
+    Alo[kmajor_off(row, k, Kp)] = 0.f;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tslot))
@@ -149,46 +149,59 @@ k_iota_C_tc(Plan<float> p, IotaDesc<float> d, const float2* __restrict__ T2, int
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = *tslot;
 
-  const uint32_t idesc = idesc_tf32(kMT, kNT);
+  const uint32_t idesc = idesc_tf32(kMT, Np);
   const uint32_t lbo = 128, sbo = (uint32_t)(Kp >> 2) * 128;
+  // this thread's T2 values of an item: pencil r, slots h = h0, h0 + 2, ...
+  float2 pre[kMaxKp / 4];
+  auto fetch = [&](long long item) {
+    const int f = (int)(item / ntn);
+    const long long n = (item % ntn) * kNT + r;
+    const float2* __restrict__ src = T2 + (long long)f * H1 * P + n;
+#pragma unroll
+    for (int j = 0; j < kMaxKp / 4; ++j) {
+      const int h = h0 + 2 * j;
+      pre[j] = (h < H1 && n < P) ? src[(long long)h * P] : make_float2(0.f, 0.f);
+    }
+  };
   uint32_t phase = 0;
   bool ok = true;
-  for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+  long long item = blockIdx.x;
+  if (item < nitems) fetch(item);
+  for (; item < nitems && ok; item += gridDim.x) {
     const int f = (int)(item / ntn);
     const long long n0 = (item % ntn) * kNT;
-    // 1. B tile, hi and lo
-    const float2* __restrict__ src = T2 + (long long)f * H1 * P + n0;
-    for (int idx = tid; idx < H1 * kNT; idx += kThreadsTC) {
-      const int h = idx / kNT, r = idx - h * kNT;
-      const float2 t = (n0 + r < P) ? src[(long long)h * P + r] : make_float2(0.f, 0.f);
-      const float hr = tf32_hi(t.x), hi_ = tf32_hi(t.y);
-      const int o = kmajor_off(r, 2 * h, Kp);
-      *reinterpret_cast<float2*>(Bhi + o) = make_float2(hr, hi_);
-      *reinterpret_cast<float2*>(Blo + o) = make_float2(t.x - hr, t.y - hi_);
+    // 1. A tile, hi and lo, from the fetched registers
+#pragma unroll
+    for (int j = 0; j < kMaxKp / 4; ++j) {
+      const int h = h0 + 2 * j;
+      if (h < H1) {
+        const float hr = tf32_hi(pre[j].x), hi_ = tf32_hi(pre[j].y);
+        const int o = kmajor_off(r, 2 * h, Kp);
+        *reinterpret_cast<float2*>(Ahi + o) = make_float2(hr, hi_);
+        *reinterpret_cast<float2*>(Alo + o) = make_float2(pre[j].x - hr, pre[j].y - hi_);
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    // 2. MMAs, one issuing thread
+    // 2. MMAs, one issuing thread; everyone fetches the next item meanwhile
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int mt = 0; mt < nmt; ++mt) {
-        const uint32_t dcol = tbase + (uint32_t)(mt * kNT);
-        for (int s = 0; s < Kp / 8; ++s) {
-          const uint32_t so = (uint32_t)s * 256;
-          const uint64_t ah = smem_desc(smem_u32(Ahi[mt]) + so, lbo, sbo);
-          const uint64_t al = smem_desc(smem_u32(Alo[mt]) + so, lbo, sbo);
-          const uint64_t bh = smem_desc(smem_u32(Bhi) + so, lbo, sbo);
-          const uint64_t bl = smem_desc(smem_u32(Blo) + so, lbo, sbo);
-          mma_tf32(dcol, ah, bh, idesc, s > 0 ? 1u : 0u);
-          mma_tf32(dcol, ah, bl, idesc, 1u);
-          mma_tf32(dcol, al, bh, idesc, 1u);
-        }
+      for (int s = 0; s < Kp / 8; ++s) {
+        const uint32_t so = (uint32_t)s * 256;
+        const uint64_t ah = smem_desc(smem_u32(Ahi) + so, lbo, sbo);
+        const uint64_t al = smem_desc(smem_u32(Alo) + so, lbo, sbo);
+        const uint64_t bh = smem_desc(smem_u32(Bhi) + so, lbo, sbo);
+        const uint64_t bl = smem_desc(smem_u32(Blo) + so, lbo, sbo);
+        mma_tf32(tbase, ah, bh, idesc, s > 0 ? 1u : 0u);
+        mma_tf32(tbase, ah, bl, idesc, 1u);
+        mma_tf32(tbase, al, bh, idesc, 1u);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        smem_u32(mbar))
                    : "memory");
     }
-    // 3. wait for the MMAs (bounded), then read D and store
+    if (item + gridDim.x < nitems) fetch(item + gridDim.x);
+    // 3. wait for the MMAs (bounded), then store D from registers
     long long it = 0;
     while (!mbar_try_wait(smem_u32(mbar), phase)) {
       if (++it > kWaitLimit) {
@@ -203,24 +216,18 @@ k_iota_C_tc(Plan<float> p, IotaDesc<float> d, const float2* __restrict__ T2, int
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // each warp reads 16 columns of its 32-lane quadrant into a padded shared
-    // tile; then every warp stores 32 consecutive floats of one row of out
+    // warp w reads lane quadrant w % 4 (pencils n0 + 32 (w % 4) + lane) and
+    // every other 16-column chunk of x1, starting at 16 (w / 4)
     const int q = warp & 3, half = warp >> 2;
-    const int r = 32 * q + (tid & 31);
-    for (int mt = 0; mt < nmt; ++mt) {
-      for (int c0 = 0; c0 < kNT; c0 += 32) {
-        float v[16];
-        tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * kNT + c0 + 16 * half), v);
+    const long long n = n0 + 32 * q + (tid & 31);
+    float* __restrict__ dst = d.dst[f] + n;
+    for (int c = 16 * half; c < Np; c += 32) {
+      float v[16];
+      tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+      if (n < P) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) stile[r * 33 + 16 * half + j] = v[j];
-        __syncthreads();
-        for (int e = tid; e < kMT * 32; e += kThreadsTC) {
-          const int row = e >> 5, col = e & 31;
-          const int x1 = mt * kMT + row;
-          const long long n = n0 + c0 + col;
-          if (x1 < G1 && n < P) d.dst[f][(long long)x1 * P + n] = stile[row * 33 + col];
-        }
-        __syncthreads();
+        for (int j = 0; j < 16; ++j)
+          if (c + j < G1) dst[(long long)(c + j) * P] = v[j];
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -235,22 +242,23 @@ k_iota_C_tc(Plan<float> p, IotaDesc<float> d, const float2* __restrict__ T2, int
 
 }  // namespace
 
-size_t iota_C_tc_smem(int K1) {
+static int tc_np(int G1) { return ((G1 + 15) / 16) * 16; }
+
+size_t iota_C_tc_smem(int K1, int G1) {
   const int Kp = ((K1 + 7) / 8) * 8;
-  return (size_t)(4 * kMT * Kp + 2 * kNT * Kp + kStile) * sizeof(float) + 16;
+  return (size_t)(2 * kMT * Kp + 2 * tc_np(G1) * Kp) * sizeof(float) + 16;
 }
 
 bool iota_C_tc_supported(const Plan<float>& p) {
   const int Kp = ((2 * p.b.h1 + 7) / 8) * 8;
-  return p.g.n1 <= 2 * kMT && Kp <= kMaxKp && iota_C_tc_smem(2 * p.b.h1) <= 200 * 1024;
+  return tc_np(p.g.n1) <= 256 && Kp <= kMaxKp && iota_C_tc_smem(2 * p.b.h1, p.g.n1) <= 200 * 1024;
 }
 
 cudaError_t iota_C_tc(const Plan<float>& p, const IotaDesc<float>& d, const float2* T2, double* flag,
                       cudaStream_t st) {
   const int Kp = ((2 * p.b.h1 + 7) / 8) * 8;
-  const int nmt = (p.g.n1 + kMT - 1) / kMT;
   // at least 96 KB per CTA: at most two CTAs (two 256-column TMEM allocations) per SM
-  const size_t smem = std::max<size_t>(iota_C_tc_smem(2 * p.b.h1), 96 * 1024 + 16);
+  const size_t smem = std::max<size_t>(iota_C_tc_smem(2 * p.b.h1, p.g.n1), 96 * 1024 + 16);
   cudaError_t e = cudaFuncSetAttribute(k_iota_C_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
@@ -259,7 +267,7 @@ cudaError_t iota_C_tc(const Plan<float>& p, const IotaDesc<float>& d, const floa
   const long long P = (long long)p.g.n2 * p.g.n3;
   const long long items = (long long)d.nf * ((P + kNT - 1) / kNT);
   const unsigned grid = (unsigned)std::min<long long>(items, 2LL * sms);
-  k_iota_C_tc<<<grid, kThreadsTC, smem, st>>>(p, d, T2, Kp, nmt, flag);
+  k_iota_C_tc<<<grid, kThreadsTC, smem, st>>>(p, d, T2, Kp, tc_np(p.g.n1), flag);
   return cudaGetLastError();
 }
 
