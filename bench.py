@@ -484,12 +484,62 @@ def run_population(args):
     print(json.dumps(line), flush=True)
 
 
+BAND_SWEEP = (16, 32, 40, 48, 56, 64)
+
+
+def run_band_sweep(args):
+    """Band-size sweep on the 160x192x160 brain phantom (a synthetic analogue of the
+    paper's band-size tables): for each K^3 band, a GN-Krylov solve from v0 = 0
+    (``--steps`` GN iterations x 10 PCG), reporting MSE_rel = 100 ||m(1) - I1||^2 /
+    ||I0 - I1||^2, the relative infinity norm of the gradient, the device memory the
+    context holds and the solve time (host clock between device synchronisations)."""
+    import numpy as np
+    import torch
+
+    from paper_1807_11560_gb300 import Context, inputs
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    kind, Ns, _, Nt, seed = workload("3d_160x192x160_brain")
+    I0, I1 = inputs.make_pair(kind, Ns, seed)
+    I0d = torch.as_tensor(I0, dtype=torch.float32, device="cuda")
+    I1d = torch.as_tensor(I1, dtype=torch.float32, device="cuda")
+    d01 = float(torch.sum((I0d - I1d) ** 2))
+    rows = []
+    for k in BAND_SWEEP:
+        Ks = (k, k, k)
+        ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision="fp32")
+        ctx.set_images(I0d, I1d)
+        v = torch.zeros((3,) + Ks, dtype=torch.complex64, device="cuda")
+        g = torch.empty_like(v)
+        ctx.gradient(v, g)
+        g0 = float(g.abs().max())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = ctx.gn_solve(v, args.steps, 10)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        m1 = torch.empty_like(I0d)
+        ctx.transport(v, m1)
+        ctx.gradient(v, g)
+        rows.append({"K": k, "mse_rel_pct": 100.0 * float(torch.sum((m1 - I1d) ** 2)) / d01,
+                     "grad_inf_rel": float(g.abs().max()) / g0, "device_gib": ctx.device_bytes / 2**30,
+                     "solve_s": t, "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters"],
+                     "hessvec_per_s": rep["pcg_iters"] / t, "tiles": ctx.tiles})
+        ctx.close()
+        print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"workload": "band_sweep_160x192x160", "Nt": Nt, "gn": args.steps, "pcg_per_gn": 10,
+                      "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "population_32":
         run_population(args)
+    elif args.workload == "band_sweep":
+        run_band_sweep(args)
     else:
         run_gpu(args)
 
