@@ -99,6 +99,26 @@ class Problem:
         W0 = sweeps.adjoint_jacobi_backward(vs, vstar, U1, self.alpha, self.s)
         return Linearisation(v0, vs, vstar, vgrid, ms, feet, E, v0 + W0)
 
+    def exact_gradient(self, v0):
+        """V-gradient of the discretised energy itself (the PDE-LDDMM route of
+        Section 2.5 in discrete form: the state transport reversed step by step,
+        Eqs. 12-14, then every time level's velocity sensitivity carried back to
+        v0 through the transpose of the Heun shoot).  Returns (E, g).
+
+        lambda(1) = dL/dm(1) = 2 sigma^-2 h^d (m(1) - I1) on the grid; the grid
+        sensitivities G_n = dL/dv_n(grid) come from ``transport_adjoint``; their
+        band V-representers are s_n = K~ sum_x G_n(x) e^{-2 pi i k.x} (the adjoint
+        of iota is N^d pi); g = v0 + W_0 with W from ``transpose_shoot``."""
+        v0 = np.asarray(v0, dtype=np.complex128)
+        vs, vstar, vgrid, ms, feet = self.forward(v0)
+        E = 0.5 * self.inner_V(v0, v0) + self.data_term(ms[-1])
+        lam1 = 2.0 * self.hd / self.sigma ** 2 * (ms[-1] - self.I1)
+        G = sweeps.transport_adjoint(ms, vgrid, lam1, self.dt)
+        nd = float(np.prod(self.Ns))
+        sources = [nd * bl.pi(Gn, self.Ks) / self.L for Gn in G]
+        W0 = sweeps.transpose_shoot(vs, vstar, sources, self.alpha, self.s)
+        return E, v0 + W0
+
     # ---- Gauss-Newton Hessian-vector product -----------------------------
     def incremental_m1(self, lin, p):
         """dm(1) from Eq. 30 (BL tangent shoot from p) and Eq. 31 (grid transport)."""

@@ -197,6 +197,98 @@ def foot_points(v_next, v_cur, dt):
     return I - 0.5 * dt * (v_next + u) * scale
 
 
+def interp_adjoint(g, xi, Ns):
+    """Transpose of ``interp`` in its grid argument: scatter g(x) with the same
+    corner weights onto the grid (the discrete counterpart of the backward
+    lambda transport of Eq. 13)."""
+    d = len(Ns)
+    i0 = [np.floor(xi[j]) for j in range(d)]
+    w = [xi[j] - i0[j] for j in range(d)]
+    i0 = [i0[j].astype(np.int64) for j in range(d)]
+    out = np.zeros(Ns)
+    for corner in itertools.product((0, 1), repeat=d):
+        idx = tuple(((i0[j] + corner[j]) % Ns[j]).ravel() for j in range(d))
+        wt = np.ones(xi.shape[1:])
+        for j in range(d):
+            wt = wt * (w[j] if corner[j] else 1.0 - w[j])
+        np.add.at(out, idx, (wt * g).ravel())
+    return out
+
+
+def interp_gradient(f, xi):
+    """Derivatives of the multilinear interpolant of f at index coords xi with
+    respect to each coordinate (exact inside a cell; the lower cell's value at
+    a node).  Returns (d, ...)."""
+    Ns = f.shape
+    d = len(Ns)
+    i0 = [np.floor(xi[j]) for j in range(d)]
+    w = [xi[j] - i0[j] for j in range(d)]
+    i0 = [i0[j].astype(np.int64) for j in range(d)]
+    out = np.zeros((d,) + xi.shape[1:])
+    for corner in itertools.product((0, 1), repeat=d):
+        idx = tuple((i0[j] + corner[j]) % Ns[j] for j in range(d))
+        fc = f[idx]
+        for a in range(d):
+            wt = np.ones(xi.shape[1:])
+            for j in range(d):
+                if j == a:
+                    wt = wt * (1.0 if corner[j] else -1.0)
+                else:
+                    wt = wt * (w[j] if corner[j] else 1.0 - w[j])
+            out[a] = out[a] + wt * fc
+    return out
+
+
+def transport_adjoint(ms, vgrid, lam1, dt):
+    """Exact reverse-mode derivative of ``transport`` (the discrete adjoint of
+    the state equation, Eqs. 12-13).
+
+    ``lam1``: dL/dm_Nt on the grid.  Returns G[n] = dL/dvgrid[n], n = 0..Nt,
+    each (d, N..), through every dependence of the semi-Lagrangian step
+        xi(x) = x - dt v_{n+1}(x),  u(x) = v_n(xi(x)),
+        X(x)  = x - dt/2 [v_{n+1}(x) + u(x)],  m_{n+1}(x) = m_n(X(x))
+    (index units: velocities scaled by N_j)."""
+    Nt = len(vgrid) - 1
+    Ns = ms[0].shape
+    d = len(Ns)
+    I = _index_grid(Ns)
+    scale = np.array(Ns, dtype=np.float64).reshape((d,) + (1,) * d)
+    G = [np.zeros((d,) + Ns) for _ in range(Nt + 1)]
+    lam = np.array(lam1, dtype=np.float64)
+    for n in range(Nt - 1, -1, -1):
+        vn, vc = vgrid[n + 1], vgrid[n]
+        xi1 = I - dt * vn * scale
+        u = np.stack([interp(vc[j], xi1) for j in range(d)])
+        X = I - 0.5 * dt * (vn + u) * scale
+        mu = lam[None] * interp_gradient(ms[n], X)          # dL/dX
+        alpha = -0.5 * dt * scale * mu                       # dL/du and the direct dL/dv_{n+1}
+        G[n + 1] += alpha
+        beta = np.zeros((d,) + Ns)                           # dL/dxi
+        for j in range(d):
+            G[n][j] += interp_adjoint(alpha[j], xi1, Ns)
+            beta += alpha[j][None] * interp_gradient(vc[j], xi1)
+        G[n + 1] += -dt * scale * beta
+        lam = interp_adjoint(lam, X, Ns)
+    return G
+
+
+def transpose_shoot(vs, vstar, sources, alpha, s):
+    """V-transpose of the Heun shoot tangent with a source at every time level:
+    W_Nt = s_Nt;  W_n = T_n^T W_{n+1} + s_n, where T_n^T applies
+        a = F'(v*_n)^T W,  W~ = W + dt a,  b = F'(v_n)^T W~,  W + dt/2 (a + b)
+    and F'(v)^T W = ad~^dagger_W v - ad~_v W is the W part of ``_GT``.
+    Returns W_0."""
+    Nt = len(vstar)
+    dt = 1.0 / Nt
+    W = np.array(sources[Nt], dtype=np.complex128)
+    for n in range(Nt - 1, -1, -1):
+        _, aW = _GT(vstar[n], np.zeros_like(W), W, alpha, s)
+        Wt = W + dt * aW
+        _, bW = _GT(vs[n], np.zeros_like(W), Wt, alpha, s)
+        W = W + 0.5 * dt * (aW + bW) + sources[n]
+    return W
+
+
 def transport(I0, vgrid, dt):
     """Semi-Lagrangian state transport (Eq. 52): m_{n+1}(x) = m_n(X_n(x)).
 
