@@ -159,6 +159,20 @@ int lddmm_energy(lddmm_ctx* ctx, const void* v0, double* E_out);
  * if E_out is not NULL, E(v0).  Sets the linearisation point for hessvec. */
 int lddmm_gradient(lddmm_ctx* ctx, const void* v0, void* g_out, double* E_out);
 
+/* V-gradient of the discretised energy itself: the route of Section 2.5
+ * (Eqs. 12-14) in discrete form, as a cross-check of the paper-form Jacobi
+ * gradient.  The semi-Lagrangian state transport is reversed step by step on
+ * the image grid (lambda scattered through the interpolation weights; the
+ * characteristic's dependence on v_n and v_{n+1} through the interpolants'
+ * exact derivatives), each time level's velocity sensitivity is projected to
+ * the band (K~ times the adjoint of iota), and the transpose of the Heun shoot
+ * carries the sources back to v0.  Same arguments and outputs as
+ * lddmm_gradient (g_out in the V representation, *E_out the energy; the
+ * linearisation point for lddmm_hessvec is set too).  Atomic scatters make the
+ * FP rounding order vary from run to run.  Needs opts.recompute = 0
+ * (LDDMM_EINVAL otherwise). */
+int lddmm_exact_gradient(lddmm_ctx* ctx, const void* v0, void* g_out, double* E_out);
+
 /* Gauss-Newton Hessian-vector product in V at the last gradient point
  * (Eqs. 30-31 and 56-58 with every adjoint-weighted term dropped, Section 2.7):
  * incremental BL EPDiff from dv, incremental state transport on the grid,

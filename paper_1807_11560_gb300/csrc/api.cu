@@ -80,6 +80,8 @@ struct Impl {
     *W = nullptr, *dstar = nullptr, *vin = nullptr, *vout = nullptr, *gbuf = nullptr;
   C *px = nullptr, *pr = nullptr, *pd = nullptr, *pq = nullptr, *vsol = nullptr, *vtry = nullptr;
   C* dvh = nullptr;          // [Nt+1][3][Kvol]
+  C* srcs = nullptr;         // [Nt+1][3][Kvol] band sources of the exact discrete adjoint
+  C* zero3 = nullptr;        // [3][Kvol] zeros
   T* dvgrid = nullptr;       // [Nt+1][3][Nvol]  (recompute: [2][3][Nvol])
   T *dm[2] = {nullptr, nullptr}, *sb[2] = {nullptr, nullptr};
   T* fterm = nullptr;        // [3][Nvol]
@@ -88,7 +90,7 @@ struct Impl {
   // persistent sweeps: evaluation descriptors recorded once at creation
   std::vector<EvalDesc<T>>* rec = nullptr;
   EvalDesc<T> *ev_shoot_lin = nullptr, *ev_shoot_trial = nullptr, *ev_tangent = nullptr,
-              *ev_backward = nullptr;
+              *ev_backward = nullptr, *ev_exact = nullptr;
   unsigned* bar = nullptr;
   double sweep_flops[3] = {0, 0, 0};   // algorithmic flops of one sweep per mode
   long long launches = 0;
@@ -346,6 +348,9 @@ struct Impl {
                   &vsol, &vtry})
       alloc(*b, (size_t)3 * Kvol);
     alloc(dvh, (size_t)(Nt + 1) * 3 * Kvol);
+    alloc(srcs, (size_t)(Nt + 1) * 3 * Kvol);
+    alloc(zero3, (size_t)3 * Kvol);
+    cuda(cudaMemset(zero3, 0, (size_t)3 * Kvol * sizeof(C)), "memset");
     alloc(dvgrid, (opts.recompute ? 2 : (size_t)Nt + 1) * 3 * Nvol);
     for (int i = 0; i < 2; ++i) {
       alloc(dm[i], (size_t)Nvol);
@@ -382,6 +387,8 @@ struct Impl {
     upload(ev_tangent);
     backward(lin);
     upload(ev_backward);
+    backward_sources(lin);
+    upload(ev_exact);
     rec = nullptr;
     sweep_flops[PW_F] = 2.0 * Nt * (flops_iota_ab() + flops_cpw(PW_F) + flops_pi_ba(1));
     sweep_flops[PW_T] = 2.0 * Nt * (flops_iota_ab() + flops_cpw(PW_T) + flops_pi_ba(1));
@@ -614,6 +621,24 @@ struct Impl {
     check_launch("projection");
   }
 
+  // K~ sum_x f(x) e^{-2 pi i k.x} of a 3-component grid field: the V-representer
+  // of the cotangent of iota (the adjoint of iota is N pi)
+  void project_adjoint(const T* f3, C* out) {
+    PiSrc<T> ps{};
+    ps.nf = 3;
+    for (int c = 0; c < 3; ++c) ps.src[c] = f3 + c * Nvol;
+    PiEpi<T> e = epi(3, 1);
+    e.grp[0] = 0;
+    e.coef[0] = (T)1;
+    e.applyK[0] = 1;
+    add_out(e, out, 0, 1.0, {});
+    pb(PR_PI_FULL);
+    pi_batch<T>(full, ps, e, Lhat, T2, st);
+    pe(PR_PI_FULL, iota_flops(3));
+    launches += kPiLaunches;
+    check_launch("projection");
+  }
+
   // ------------------------------------------------------------- sweeps
   T* slot(State<T>& S, int k) { return S.cache + (long long)k * cache_slot_elems<T>(pad); }
   C* vec(C* base, int n) { return base + (long long)n * 3 * Kvol; }
@@ -753,6 +778,82 @@ struct Impl {
     }
   }
 
+  // transpose of the Heun shoot tangent with a band source at every time level
+  // (the exact discrete adjoint's band sweep): W_Nt = s_Nt, W_n = T_n^T W_{n+1}
+  // + s_n with T_n^T the W part of the backward Jacobi sweep (U = 0); leaves
+  // W_0 in W
+  void backward_sources(State<T>& S) {
+    const double m = 1.0 / (double)Mvol;
+    if (!rec)
+      cuda(cudaMemcpyAsync(W, srcs + (long long)Nt * 3 * Kvol, (size_t)3 * Kvol * sizeof(C),
+                           cudaMemcpyDeviceToDevice, st), "copy source");
+    if (persistent()) {
+      run_sweep(PW_GT, ev_exact);
+      return;
+    }
+    for (int n = Nt - 1; n >= 0; --n) {
+      PiEpi<T> e1 = epi(3, 3);
+      e1.grp[0] = 0; e1.coef[0] = (T)0;  e1.applyK[0] = 1;   // (U = 0)
+      e1.grp[1] = 1; e1.coef[1] = (T)m;  e1.applyK[1] = 1;   // ad^dag_W v
+      e1.grp[2] = 1; e1.coef[2] = (T)-m; e1.applyK[2] = 0;   // -ad_v W
+      add_out(e1, aW, 1, 1.0, {});
+      add_out(e1, Wt, 1, dt, {{W, 1.0}});
+      eval(PW_GT, slot(S, 2 * n + 1), W, zero3, e1);
+      PiEpi<T> e2 = epi(3, 3);
+      e2.grp[0] = 0; e2.coef[0] = (T)0;  e2.applyK[0] = 1;
+      e2.grp[1] = 1; e2.coef[1] = (T)m;  e2.applyK[1] = 1;
+      e2.grp[2] = 1; e2.coef[2] = (T)-m; e2.applyK[2] = 0;
+      add_out(e2, W, 1, 0.5 * dt, {{W, 1.0}, {aW, 0.5 * dt}, {srcs + (long long)n * 3 * Kvol, 1.0}});
+      eval(PW_GT, slot(S, 2 * n), Wt, zero3, e2);
+    }
+  }
+
+  // V-gradient of the discretised energy itself (Section 2.5's route in
+  // discrete form, Eqs. 12-14): the state transport reversed step by step on
+  // the image grid, each time level's velocity sensitivity projected to the
+  // band, then carried back to v0 by backward_sources.  Needs the kept
+  // histories (every reversed step reads m_n, v_n, v_{n+1} and the displacement
+  // in reverse time order).
+  double exact_gradient_dev(const C* v0dev, C* gdev) {
+    need_images();
+    if (opts.recompute) {
+      *err = "the exact discrete adjoint reads the histories in reverse: create the context with recompute = 0";
+      throw Fail{LDDMM_EINVAL};
+    }
+    cuda(cudaMemcpyAsync(lin.vh, v0dev, (size_t)3 * Kvol * sizeof(C), cudaMemcpyDeviceToDevice, st),
+         "copy v0");
+    forward(lin);
+    energy_terms(lin);
+    T* lam_next = dm[0];
+    T* lam_cur = dm[1];
+    T* Gn = dvgrid;                       // G[n+1]
+    T* Gc = dvgrid + 3 * Nvol;            // G[n]
+    const size_t gbytes = (size_t)3 * Nvol * sizeof(T);
+    scaled_diff<T>(m1(lin), I1, 2.0 / (sigma * sigma * (double)Nvol), lam_next, Nvol, st);
+    cuda(cudaMemsetAsync(Gn, 0, gbytes, st), "memset");
+    cuda(cudaMemsetAsync(Gc, 0, gbytes, st), "memset");
+    ++launches;
+    for (int n = Nt - 1; n >= 0; --n) {
+      cuda(cudaMemsetAsync(lam_cur, 0, (size_t)Nvol * sizeof(T), st), "memset");
+      adjoint_step<T>(lam_next, mstate(lin, n), vgr(lin, n), vgr(lin, n + 1), offp(lin, n), lam_cur, Gn, Gc,
+                      N, dt, st);
+      ++launches;
+      project_adjoint(Gn, srcs + (long long)(n + 1) * 3 * Kvol);   // G[n+1] is complete
+      std::swap(Gn, Gc);
+      cuda(cudaMemsetAsync(Gc, 0, gbytes, st), "memset");
+      std::swap(lam_next, lam_cur);
+    }
+    project_adjoint(Gn, srcs);
+    backward_sources(lin);
+    axpby<T>(gdev, 1.0, lin.vh, 1.0, W, 3 * Kvol, st);
+    ++launches;
+    check_launch("exact gradient");
+    const double E = read_energy();
+    have_lin = true;
+    have_dm1 = false;
+    return E;
+  }
+
   // enqueue one GN Hessian-vector product: input dvh[0], output vout
   void enqueue_hessvec() {
     State<T>& S = lin;
@@ -848,6 +949,14 @@ struct Impl {
     const double E = gradient_dev(vsol, gbuf);
     store_bl(gbuf, g);
     sync("gradient output");
+    return E;
+  }
+
+  double exact_gradient(const void* v0, void* g) {
+    load_bl(v0, vsol);
+    const double E = exact_gradient_dev(vsol, gbuf);
+    store_bl(gbuf, g);
+    sync("exact gradient output");
     return E;
   }
 
@@ -1265,6 +1374,15 @@ int lddmm_gradient(lddmm_ctx* ctx, const void* v0, void* g, double* E) {
   if (bad_ptr(ctx, v0, "v0") || bad_ptr(ctx, g, "g_out")) return LDDMM_EINVAL;
   return lddmm::dispatch(ctx, [&](auto& im) {
     const double e = im.gradient(v0, g);
+    if (E) *E = e;
+  });
+}
+
+int lddmm_exact_gradient(lddmm_ctx* ctx, const void* v0, void* g, double* E) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, v0, "v0") || bad_ptr(ctx, g, "g_out")) return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) {
+    const double e = im.exact_gradient(v0, g);
     if (E) *E = e;
   });
 }

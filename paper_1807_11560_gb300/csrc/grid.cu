@@ -152,6 +152,92 @@ k_inc_step(const T* __restrict__ dm, const T* __restrict__ s, const T* __restric
   sn[idx] = snew;
 }
 
+// weights of the 8 cell corners in the order of corners(); w = upper-node weights
+template <typename T>
+__device__ __forceinline__ void corner_weights(const T* w, T* c) {
+  const T a0 = T(1) - w[0], a1 = T(1) - w[1], a2 = T(1) - w[2];
+  c[0] = a0 * a1 * a2;
+  c[1] = a0 * a1 * w[2];
+  c[2] = a0 * w[1] * a2;
+  c[3] = a0 * w[1] * w[2];
+  c[4] = w[0] * a1 * a2;
+  c[5] = w[0] * a1 * w[2];
+  c[6] = w[0] * w[1] * a2;
+  c[7] = w[0] * w[1] * w[2];
+}
+
+// derivatives of the trilinear interpolant (corner values f) with respect to
+// the three index coordinates, inside the cell of upper-node weights w
+template <typename T>
+__device__ __forceinline__ void trilin_grad(const T* f, const T* w, T* g) {
+  const T a0 = T(1) - w[0], a1 = T(1) - w[1], a2 = T(1) - w[2];
+  g[0] = a1 * (a2 * (f[4] - f[0]) + w[2] * (f[5] - f[1])) + w[1] * (a2 * (f[6] - f[2]) + w[2] * (f[7] - f[3]));
+  g[1] = a0 * (a2 * (f[2] - f[0]) + w[2] * (f[3] - f[1])) + w[0] * (a2 * (f[6] - f[4]) + w[2] * (f[7] - f[5]));
+  g[2] = a0 * (a1 * (f[1] - f[0]) + w[1] * (f[3] - f[2])) + w[0] * (a1 * (f[5] - f[4]) + w[1] * (f[7] - f[6]));
+}
+
+// One step of the exact discrete adjoint of the state transport (the
+// semi-Lagrangian form of Eq. 13, reversed): with xi = x - dt v_{n+1}(x),
+// u = v_n(xi), X = x - dt/2 (v_{n+1}(x) + u) and m_{n+1}(x) = m_n(X),
+//   lam_n      += scatter of lam_{n+1}(x) at X            (atomic)
+//   G_n        += scatter of alpha(x) at xi                (atomic)
+//   G_{n+1}(x) += alpha - dt N (sum_j alpha_j d v_n,j(xi)/d xi)
+// where alpha = -dt/2 N lam_{n+1}(x) d m_n(X)/dX (index units, N per axis).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_adj_step(const T* __restrict__ lam, const T* __restrict__ m, const T* __restrict__ vc,
+           const T* __restrict__ vn, const T* __restrict__ off, T* __restrict__ lam_out,
+           T* __restrict__ gnext, T* __restrict__ gcur, Dims g, T dt) {
+  const long long vol = g.vol();
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= vol) return;
+  int ix[3];
+  unflat(idx, g.n2, g.n3, ix);
+  const int n[3] = {g.n1, g.n2, g.n3};
+  const T l = lam[idx];
+  int c0[3], c1[3], o[8];
+  T w[3], cw[8], f[8], d[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) cell(ix[j], off[j * vol + idx], n[j], c0[j], c1[j], w[j]);
+  corners(c0, c1, g.n2, g.n3, o);
+  corner_weights(w, cw);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    f[c] = m[o[c]];
+    atomicAdd(lam_out + o[c], cw[c] * l);
+  }
+  trilin_grad(f, w, d);
+  T alpha[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) alpha[j] = T(-0.5) * dt * T(n[j]) * l * d[j];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) cell(ix[j], dt * T(n[j]) * vn[j * vol + idx], n[j], c0[j], c1[j], w[j]);
+  corners(c0, c1, g.n2, g.n3, o);
+  corner_weights(w, cw);
+  T beta[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const T* __restrict__ vj = vc + j * vol;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      f[c] = vj[o[c]];
+      atomicAdd(gcur + j * vol + o[c], cw[c] * alpha[j]);
+    }
+    trilin_grad(f, w, d);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) beta[i] = fma(alpha[j], d[i], beta[i]);
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) gnext[j * vol + idx] += alpha[j] - dt * T(n[j]) * beta[j];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_scaled_diff(const T* __restrict__ a, const T* __restrict__ b, T c, T* __restrict__ out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = c * (a[i] - b[i]);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_terminal(const T* __restrict__ m, const T* __restrict__ y, int diff, T coef, T* __restrict__ out,
@@ -282,6 +368,18 @@ void inc_step(const T* dm, const T* s, const T* mnext, const T* dvnext, const T*
 }
 
 template <typename T>
+void adjoint_step(const T* lam, const T* m, const T* vcur, const T* vnext, const T* off, T* lam_out, T* gnext,
+                  T* gcur, Dims g, double dt, cudaStream_t st) {
+  k_adj_step<T><<<blocks_for(g.vol()), kThreads, 0, st>>>(lam, m, vcur, vnext, off, lam_out, gnext, gcur, g,
+                                                         (T)dt);
+}
+
+template <typename T>
+void scaled_diff(const T* a, const T* b, double c, T* out, long long n, cudaStream_t st) {
+  k_scaled_diff<T><<<blocks_for(n), kThreads, 0, st>>>(a, b, (T)c, out, n);
+}
+
+template <typename T>
 void terminal_field(const T* m, const T* y, int diff, double coef, T* out, Dims g, cudaStream_t st) {
   k_terminal<T><<<blocks_for(g.vol()), kThreads, 0, st>>>(m, y, diff, (T)coef, out, g);
 }
@@ -322,6 +420,9 @@ void inner_V(const cplx<T>* a, const cplx<T>* b, const T* Lhat, int ncomp, long 
   template void inc_step<T>(const T*, const T*, const T*, const T*, const T*, T*, T*, Dims,      \
                             double, cudaStream_t);                                               \
   template void terminal_field<T>(const T*, const T*, int, double, T*, Dims, cudaStream_t);      \
+  template void adjoint_step<T>(const T*, const T*, const T*, const T*, const T*, T*, T*, T*, Dims,  \
+                                double, cudaStream_t);                                              \
+  template void scaled_diff<T>(const T*, const T*, double, T*, long long, cudaStream_t);          \
   template void hermitianize<T>(const cplx<T>*, cplx<T>*, int, Band, cudaStream_t);             \
   template void axpby<T>(cplx<T>*, double, const cplx<T>*, double, const cplx<T>*, long long,    \
                          cudaStream_t);                                                          \

@@ -192,6 +192,15 @@ void inc_step(const T* dm, const T* s, const T* mnext, const T* dvnext, const T*
 template <typename T>
 void terminal_field(const T* m, const T* y, int diff, double coef, T* out, Dims g,
                     cudaStream_t st);
+// one reversed step of the exact discrete adjoint of the state transport:
+// lam_out (zeroed by the caller) and gcur gain atomic scatters, gnext gains the
+// per-voxel terms (see grid.cu); off is the step's stored displacement.
+template <typename T>
+void adjoint_step(const T* lam, const T* m, const T* vcur, const T* vnext, const T* off, T* lam_out, T* gnext,
+                  T* gcur, Dims g, double dt, cudaStream_t st);
+// out = c (a - b)
+template <typename T>
+void scaled_diff(const T* a, const T* b, double c, T* out, long long n, cudaStream_t st);
 
 // ---- band vectors and reductions (grid.cu) --------------------------------
 template <typename T>

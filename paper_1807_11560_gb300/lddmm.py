@@ -106,6 +106,7 @@ def lib():
         "lddmm_energy": (I, [P, P, ctypes.POINTER(D)]),
         "lddmm_gradient": (I, [P, P, P, ctypes.POINTER(D)]),
         "lddmm_hessvec": (I, [P, P, P]),
+        "lddmm_exact_gradient": (I, [P, P, P, ctypes.POINTER(D)]),
         "lddmm_gn_solve": (I, [P, P, I, I, ctypes.POINTER(Report)]),
         "lddmm_batch_gn_solve": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P), I, I,
                                      ctypes.POINTER(Report), I]),
@@ -250,6 +251,13 @@ class Context:
         E = ctypes.c_double()
         self._check(lib().lddmm_gradient(self._h, self._arg(v0, "cplx", self.nband),
                                          self._arg(g_out, "cplx", self.nband), ctypes.byref(E)))
+        return E.value
+
+    def exact_gradient(self, v0, g_out):
+        """V-gradient of the discretised energy (exact discrete adjoint); returns E."""
+        E = ctypes.c_double()
+        self._check(lib().lddmm_exact_gradient(self._h, self._arg(v0, "cplx", self.nband),
+                                               self._arg(g_out, "cplx", self.nband), ctypes.byref(E)))
         return E.value
 
     def hessvec(self, dv, out):
