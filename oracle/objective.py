@@ -135,6 +135,32 @@ class Problem:
         dW0 = sweeps.adjoint_jacobi_backward(lin.vs, lin.vstar, dU1, self.alpha, self.s)
         return p + dW0
 
+    def terminal_U_newton(self, m1, dm1):
+        """Derivative of U~(1) = K~ pi(lambda(1) grad m(1)) along dm(1):
+        K~ pi(dlambda(1) grad m(1) + lambda(1) grad dm(1)), lambda(1) = -(2/sigma^2)
+        (m(1) - I1), dlambda(1) = -(2/sigma^2) dm(1) (Eq. 58 without the
+        Gauss-Newton drop; the sign of the second term follows from differentiating
+        the gradient's own terminal value)."""
+        c = -2.0 / self.sigma ** 2
+        f = c * (dm1[None] * sweeps.central_grad(m1) + (m1 - self.I1)[None] * sweeps.central_grad(dm1))
+        return bl.pi(f, self.Ks) / self.L
+
+    def hessvec_newton(self, lin, p):
+        """Full-Newton Hessian-vector product in V (Eqs. 56-58 without the
+        Gauss-Newton drop): the derivative of the paper-form gradient
+        g = v0 + W(0)[v; U~(1)] along p, with dm(1) from the incremental state
+        sweep (Eq. 31) as in the Gauss-Newton product.  H p = p + dW(0)."""
+        p = np.asarray(p, dtype=np.complex128)
+        dvs, dstar = sweeps.tangent_shoot_stages(lin.vs, lin.vstar, p, self.alpha, self.s)
+        dvgrid = [self.grid_velocity(d) for d in dvs]
+        dm1 = sweeps.incremental_transport(lin.ms, lin.feet, dvgrid, self.dt)
+        dU1 = self.terminal_U_newton(lin.ms[-1], dm1)
+        m1 = lin.ms[-1]
+        U1 = self.terminal_U(m1, -(2.0 / self.sigma ** 2) * (m1 - self.I1))
+        _, zs, zt = sweeps.adjoint_jacobi_backward_stages(lin.vs, lin.vstar, U1, self.alpha, self.s)
+        dW0 = sweeps.newton_backward(lin.vs, lin.vstar, dvs, dstar, zs, zt, dU1, self.alpha, self.s)
+        return p + dW0
+
     def hessvec_J(self, lin, p):
         """Diagnostic J-form GN product: dm(1) replaced by -grad m(1) . iota(J(1)).
 

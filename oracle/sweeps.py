@@ -37,7 +37,8 @@ from . import bl
 
 __all__ = [
     "epdiff_rhs", "epdiff_rhs_tangent", "shoot", "tangent_shoot",
-    "jacobi_tangent", "adjoint_jacobi_backward", "interp", "central_grad",
+    "jacobi_tangent", "adjoint_jacobi_backward", "adjoint_jacobi_backward_stages",
+    "tangent_shoot_stages", "newton_backward", "interp", "central_grad",
     "foot_points", "transport", "incremental_transport",
 ]
 
@@ -92,6 +93,22 @@ def tangent_shoot(vs, vstar, p, alpha, s):
     return out
 
 
+def tangent_shoot_stages(vs, vstar, p, alpha, s):
+    """``tangent_shoot`` with its stage values: (dvs[n] for n = 0..Nt, dstar[n] =
+    the tangent of the predictor v*_n)."""
+    Nt = len(vstar)
+    dt = 1.0 / Nt
+    dvs, dstar = [np.array(p, dtype=np.complex128)], []
+    for n in range(Nt):
+        d = dvs[-1]
+        k1 = epdiff_rhs_tangent(vs[n], d, alpha, s)
+        dp = d + dt * k1
+        k2 = epdiff_rhs_tangent(vstar[n], dp, alpha, s)
+        dstar.append(dp)
+        dvs.append(d + 0.5 * dt * (k1 + k2))
+    return dvs, dstar
+
+
 def _G(v, J, dv, alpha, s):
     """Right side of the Jacobi-field tangent: (dv + ad~_v J, linearised EPDiff)."""
     return dv + bl.ad(v, J), epdiff_rhs_tangent(v, dv, alpha, s)
@@ -143,6 +160,60 @@ def adjoint_jacobi_backward(vs, vstar, U1, alpha, s):
         U = U + 0.5 * dt * (aU + bU)
         W = W + 0.5 * dt * (aW + bW)
     return W
+
+
+def adjoint_jacobi_backward_stages(vs, vstar, U1, alpha, s):
+    """``adjoint_jacobi_backward`` with its stage values: (W(0), zs, zt) where
+    zs[n] = (U, W) at time level n (n = 0..Nt) and zt[n] = the stage value
+    (U~, W~) of step n -> n-1 ... i.e. z~ = z_{n+1} + dt a of step n."""
+    Nt = len(vstar)
+    dt = 1.0 / Nt
+    U = np.array(U1, dtype=np.complex128)
+    W = np.zeros_like(U)
+    zs = [None] * (Nt + 1)
+    zt = [None] * Nt
+    zs[Nt] = (U, W)
+    for n in range(Nt - 1, -1, -1):
+        aU, aW = _GT(vstar[n], U, W, alpha, s)
+        Ut, Wt = U + dt * aU, W + dt * aW
+        zt[n] = (Ut, Wt)
+        bU, bW = _GT(vs[n], Ut, Wt, alpha, s)
+        U = U + 0.5 * dt * (aU + bU)
+        W = W + 0.5 * dt * (aW + bW)
+        zs[n] = (U, W)
+    return W, zs, zt
+
+
+def _Gp(dv, U, W, alpha, s):
+    """Derivative of ``_GT`` with respect to its velocity along dv (the terms the
+    Gauss-Newton form drops from Eqs. 56-57): (ad~^dagger_dv U,
+    ad~^dagger_W dv - ad~_dv W)."""
+    return (bl.ad_dagger(dv, U, alpha, s),
+            bl.ad_dagger(W, dv, alpha, s) - bl.ad(dv, W))
+
+
+def newton_backward(vs, vstar, dvs, dstar, zs, zt, dU1, alpha, s):
+    """Full-Newton incremental adjoint sweep (Eqs. 56-57 without the Gauss-Newton
+    drop): the derivative of the Heun-transposed recursion of
+    ``adjoint_jacobi_backward`` along the velocity trajectory's tangent (dvs,
+    dstar), started from (dU1, 0); the gradient sweep's stage values (zs, zt)
+    carry the dropped terms.  Returns dW(0)."""
+    Nt = len(vstar)
+    dt = 1.0 / Nt
+    dU = np.array(dU1, dtype=np.complex128)
+    dW = np.zeros_like(dU)
+    for n in range(Nt - 1, -1, -1):
+        U, W = zs[n + 1]
+        aU, aW = _GT(vstar[n], dU, dW, alpha, s)
+        gU, gW = _Gp(dstar[n], U, W, alpha, s)
+        aU, aW = aU + gU, aW + gW
+        dUt, dWt = dU + dt * aU, dW + dt * aW
+        Ut, Wt = zt[n]
+        bU, bW = _GT(vs[n], dUt, dWt, alpha, s)
+        hU, hW = _Gp(dvs[n], Ut, Wt, alpha, s)
+        dU = dU + 0.5 * dt * (aU + bU + hU)
+        dW = dW + 0.5 * dt * (aW + bW + hW)
+    return dW
 
 
 # --------------------------------------------------------------------------
