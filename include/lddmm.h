@@ -106,6 +106,9 @@ typedef struct {
                            fastest; 0: size heuristics.  Contexts whose sweeps run as
                            persistent kernels keep the heuristics.  No result depends on
                            the tile shapes. */
+  int newton;           /* Hessian used by lddmm_gn_solve's PCG: 0 Gauss-Newton (default),
+                           1 full Newton (lddmm_hessvec_newton); PCG stops at the first
+                           direction of non-positive curvature either way. */
 } lddmm_opts;
 
 /* Report of lddmm_gn_solve.  The per-iteration arrays are optional
@@ -158,6 +161,17 @@ int lddmm_energy(lddmm_ctx* ctx, const void* v0, double* E_out);
  * and the backward reduced adjoint Jacobi sweep.  Writes g (BL field) and,
  * if E_out is not NULL, E(v0).  Sets the linearisation point for hessvec. */
 int lddmm_gradient(lddmm_ctx* ctx, const void* v0, void* g_out, double* E_out);
+
+/* Full-Newton Hessian-vector product at the last lddmm_gradient point (Eqs.
+ * 56-58 without the Gauss-Newton drop): the derivative of the paper-form
+ * gradient along dv.  Adds to the Gauss-Newton product the terms carried by
+ * the adjoint variables - ad~^dagger_dv U, ad~^dagger_W dv - ad~_dv W in the
+ * backward sweep (with the gradient sweep's (U, W) at every Heun stage and the
+ * tangent's dv) and lambda(1) grad dm(1) in the terminal value.  Not symmetric
+ * and not positive definite in general.  Same arguments as lddmm_hessvec;
+ * LDDMM_ESTATE unless the last call that set the linearisation point was
+ * lddmm_gradient (or lddmm_gn_solve). */
+int lddmm_hessvec_newton(lddmm_ctx* ctx, const void* dv, void* Hdv_out);
 
 /* V-gradient of the discretised energy itself: the route of Section 2.5
  * (Eqs. 12-14) in discrete form, as a cross-check of the paper-form Jacobi

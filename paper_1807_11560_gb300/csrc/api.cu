@@ -81,6 +81,11 @@ struct Impl {
   C *px = nullptr, *pr = nullptr, *pd = nullptr, *pq = nullptr, *vsol = nullptr, *vtry = nullptr;
   C* dvh = nullptr;          // [Nt+1][3][Kvol]
   C* srcs = nullptr;         // [Nt+1][3][Kvol] band sources of the exact discrete adjoint
+  C* dvsh = nullptr;         // [Nt][3][Kvol] tangent predictor stages dv*_n
+  C *Uh = nullptr, *Wh = nullptr;     // [Nt+1][3][Kvol] gradient sweep (U, W) per time level
+  C *Uth = nullptr, *Wth = nullptr;   // [Nt][3][Kvol] gradient sweep stage values (U~, W~)
+  C *bU = nullptr, *bW = nullptr;     // full-Newton sweep scratch
+  T* tcache = nullptr;       // [2 Nt][cache_slot_elems] tangent stage-point fields (full Newton)
   C* zero3 = nullptr;        // [3][Kvol] zeros
   T* dvgrid = nullptr;       // [Nt+1][3][Nvol]  (recompute: [2][3][Nvol])
   T *dm[2] = {nullptr, nullptr}, *sb[2] = {nullptr, nullptr};
@@ -90,15 +95,17 @@ struct Impl {
   // persistent sweeps: evaluation descriptors recorded once at creation
   std::vector<EvalDesc<T>>* rec = nullptr;
   EvalDesc<T> *ev_shoot_lin = nullptr, *ev_shoot_trial = nullptr, *ev_tangent = nullptr,
-              *ev_backward = nullptr, *ev_exact = nullptr;
+              *ev_backward = nullptr, *ev_exact = nullptr, *ev_tangent_c = nullptr,
+              *ev_backward_hist = nullptr, *ev_newton = nullptr;
   unsigned* bar = nullptr;
   double sweep_flops[3] = {0, 0, 0};   // algorithmic flops of one sweep per mode
   long long launches = 0;
   std::vector<void*> allocs;
   unsigned long long device_bytes = 0;
   // graph of one Hessian-vector product (input dvh[0], output vout)
-  cudaGraphExec_t hv_exec = nullptr;
-  long long hv_nodes = 0;
+  cudaGraphExec_t hv_exec = nullptr, hv_exec_newton = nullptr;
+  long long hv_nodes = 0, hv_nodes_newton = 0;
+  bool have_zhist = false;   // Uh/Wh/Uth/Wth hold the last gradient's backward sweep
   cudaStream_t cap = nullptr;
   cudaEvent_t ev = nullptr;
   bool capturing = false;
@@ -141,6 +148,8 @@ struct Impl {
   void release() {
     if (hv_exec) cudaGraphExecDestroy(hv_exec);
     hv_exec = nullptr;
+    if (hv_exec_newton) cudaGraphExecDestroy(hv_exec_newton);
+    hv_exec_newton = nullptr;
     if (cap) cudaStreamDestroy(cap);
     cap = nullptr;
     if (ev) cudaEventDestroy(ev);
@@ -259,7 +268,7 @@ struct Impl {
       for (int tp : kTp) {
         if (!tile_valid<T>(pad, pad.tws, tp, 0)) continue;
         pad.tp = tp;
-        const float t = best_of([&] { bracket_cpw<T>(pad, PW_GT, T2, slot, P2, st); });
+        const float t = best_of([&] { bracket_cpw<T>(pad, PW_GT, T2, slot, nullptr, P2, st); });
         if (t < best) { best = t; pick = tp; }
       }
       pad.tp = pick;
@@ -349,6 +358,13 @@ struct Impl {
       alloc(*b, (size_t)3 * Kvol);
     alloc(dvh, (size_t)(Nt + 1) * 3 * Kvol);
     alloc(srcs, (size_t)(Nt + 1) * 3 * Kvol);
+    alloc(dvsh, (size_t)Nt * 3 * Kvol);
+    alloc(Uh, (size_t)(Nt + 1) * 3 * Kvol);
+    alloc(Wh, (size_t)(Nt + 1) * 3 * Kvol);
+    alloc(Uth, (size_t)Nt * 3 * Kvol);
+    alloc(Wth, (size_t)Nt * 3 * Kvol);
+    alloc(bU, (size_t)3 * Kvol);
+    alloc(bW, (size_t)3 * Kvol);
     alloc(zero3, (size_t)3 * Kvol);
     cuda(cudaMemset(zero3, 0, (size_t)3 * Kvol * sizeof(C)), "memset");
     alloc(dvgrid, (opts.recompute ? 2 : (size_t)Nt + 1) * 3 * Nvol);
@@ -364,6 +380,7 @@ struct Impl {
     if (opts.autotune && !persistent()) autotune();
     make_state(lin);                       // the cache layout follows the tile shapes
     make_state(trial);
+    alloc(tcache, (size_t)2 * Nt * cache_slot_elems<T>(pad));
     alloc(bar, kSweepBarWords);
     record_sweeps();
     cuda(cudaDeviceSynchronize(), "create");
@@ -389,6 +406,12 @@ struct Impl {
     upload(ev_backward);
     backward_sources(lin);
     upload(ev_exact);
+    tangent(lin, true);
+    upload(ev_tangent_c);
+    backward_hist(lin);
+    upload(ev_backward_hist);
+    newton_backward(lin);
+    upload(ev_newton);
     rec = nullptr;
     sweep_flops[PW_F] = 2.0 * Nt * (flops_iota_ab() + flops_cpw(PW_F) + flops_pi_ba(1));
     sweep_flops[PW_T] = 2.0 * Nt * (flops_iota_ab() + flops_cpw(PW_T) + flops_pi_ba(1));
@@ -537,16 +560,16 @@ struct Impl {
     return 8.0 * 3 * nper * H1 * (K2 * M2 * M3 + K2 * K3 * M3);
   }
 
-  void eval(PwMode mode, T* slot, const C* srcA, const C* srcB, const PiEpi<T>& e) {
+  void eval(PwMode mode, T* slot, const C* srcA, const C* srcB, const PiEpi<T>& e, T* slot2 = nullptr) {
     if (rec) {
-      rec->push_back(EvalDesc<T>{srcA, srcB, slot, e});
+      rec->push_back(EvalDesc<T>{srcA, srcB, slot, slot2, e});
       return;
     }
     pb(PR_IOTA_AB);
     bracket_iota<T>(pad, block24(srcA, srcB, slot), Lhat, T2, st);
     pe(PR_IOTA_AB, flops_iota_ab());
     pb(PR_CPW);
-    bracket_cpw<T>(pad, mode, T2, slot, P2, st);
+    bracket_cpw<T>(pad, mode, T2, slot, slot2, P2, st);
     pe(PR_CPW, flops_cpw(mode));
     pb(PR_PI_BA);
     bracket_pi<T>(pad, e, Lhat, P2, st);
@@ -556,10 +579,11 @@ struct Impl {
   }
 
   // one band-limited sweep as a single persistent cooperative kernel
-  void run_sweep(PwMode mode, const EvalDesc<T>* ev) {
+  void run_sweep(PwMode mode, const EvalDesc<T>* ev, int nev = 0) {
+    if (nev == 0) nev = 2 * Nt;
     pb(PR_SWEEP);
-    cuda(sweep_launch<T>(pad, mode, ev, 2 * Nt, Lhat, T2, P2, bar, dres + 7, st), "persistent sweep");
-    pe(PR_SWEEP, sweep_flops[mode]);
+    cuda(sweep_launch<T>(pad, mode, ev, nev, Lhat, T2, P2, bar, dres + 7, st), "persistent sweep");
+    pe(PR_SWEEP, sweep_flops[mode] * nev / (2.0 * Nt));
     ++launches;
   }
   // persistent sweeps pay off while the phases are latency-bound (small padded
@@ -753,28 +777,33 @@ struct Impl {
   }
 
   // incremental EPDiff (Eq. 30) from dvh[0], exact tangent of the Heun shoot
-  void tangent(State<T>& S) {
+  T* tslot(int k) { return tcache + (long long)k * cache_slot_elems<T>(pad); }
+
+  // incremental BL EPDiff (Eq. 30) from dvh[0]; with cache, also stores the
+  // padded-grid fields of dv_n and dv*_n (full-Newton products)
+  void tangent(State<T>& S, bool cache = false) {
     if (persistent()) {
-      run_sweep(PW_T, ev_tangent);
+      run_sweep(PW_T, cache ? ev_tangent_c : ev_tangent);
       return;
     }
     const double m = 1.0 / (double)Mvol;
     for (int n = 0; n < Nt; ++n) {
       C* dn = vec(dvh, n);
       C* dn1 = vec(dvh, n + 1);
+      C* dstar = vec(dvsh, n);
       PiEpi<T> e1 = epi(3, 1);
       e1.grp[0] = 0;
       e1.coef[0] = (T)(-m);
       e1.applyK[0] = 1;
       add_out(e1, k1, 0, 1.0, {});
       add_out(e1, dstar, 0, dt, {{dn, 1.0}});
-      eval(PW_T, slot(S, 2 * n), dn, dn, e1);
+      eval(PW_T, slot(S, 2 * n), dn, dn, e1, cache ? tslot(2 * n) : nullptr);
       PiEpi<T> e2 = epi(3, 1);
       e2.grp[0] = 0;
       e2.coef[0] = (T)(-m);
       e2.applyK[0] = 1;
       add_out(e2, dn1, 0, 0.5 * dt, {{dn, 1.0}, {k1, 0.5 * dt}});
-      eval(PW_T, slot(S, 2 * n + 1), dstar, dstar, e2);
+      eval(PW_T, slot(S, 2 * n + 1), dstar, dstar, e2, cache ? tslot(2 * n + 1) : nullptr);
     }
   }
 
@@ -805,6 +834,84 @@ struct Impl {
       e2.grp[2] = 1; e2.coef[2] = (T)-m; e2.applyK[2] = 0;
       add_out(e2, W, 1, 0.5 * dt, {{W, 1.0}, {aW, 0.5 * dt}, {srcs + (long long)n * 3 * Kvol, 1.0}});
       eval(PW_GT, slot(S, 2 * n), Wt, zero3, e2);
+    }
+  }
+
+  // the gradient's backward sweep (Eqs. 53-54) with its time levels and stage
+  // values kept: level n in (Uh[n], Wh[n]) (Uh[Nt] = U~(1) set by the caller),
+  // stage of step n in (Uth[n], Wth[n]); W(0) = Wh[0]
+  void backward_hist(State<T>& S) {
+    const double m = 1.0 / (double)Mvol;
+    if (!rec) cuda(cudaMemsetAsync(vec(Wh, Nt), 0, (size_t)3 * Kvol * sizeof(C), st), "memset W");
+    if (persistent()) {
+      run_sweep(PW_GT, ev_backward_hist);
+      return;
+    }
+    for (int n = Nt - 1; n >= 0; --n) {
+      C *U1 = vec(Uh, n + 1), *W1 = vec(Wh, n + 1), *Ut_ = vec(Uth, n), *Wt_ = vec(Wth, n);
+      PiEpi<T> e1 = epi(3, 3);
+      e1.grp[0] = 0; e1.coef[0] = (T)m;  e1.applyK[0] = 1;   // ad^dag_v U
+      e1.grp[1] = 1; e1.coef[1] = (T)m;  e1.applyK[1] = 1;   // ad^dag_W v
+      e1.grp[2] = 1; e1.coef[2] = (T)-m; e1.applyK[2] = 0;   // -ad_v W
+      add_out(e1, aU, 0, 1.0, {});
+      add_out(e1, aW, 1, 1.0, {{U1, 1.0}});
+      add_out(e1, Ut_, 0, dt, {{U1, 1.0}});
+      add_out(e1, Wt_, 1, dt, {{W1, 1.0}, {U1, dt}});
+      eval(PW_GT, slot(S, 2 * n + 1), W1, U1, e1);
+      PiEpi<T> e2 = epi(3, 3);
+      e2.grp[0] = 0; e2.coef[0] = (T)m;  e2.applyK[0] = 1;
+      e2.grp[1] = 1; e2.coef[1] = (T)m;  e2.applyK[1] = 1;
+      e2.grp[2] = 1; e2.coef[2] = (T)-m; e2.applyK[2] = 0;
+      add_out(e2, vec(Uh, n), 0, 0.5 * dt, {{U1, 1.0}, {aU, 0.5 * dt}});
+      add_out(e2, vec(Wh, n), 1, 0.5 * dt, {{W1, 1.0}, {aW, 0.5 * dt}, {Ut_, 0.5 * dt}});
+      eval(PW_GT, slot(S, 2 * n), Wt_, Ut_, e2);
+    }
+  }
+
+  // full-Newton incremental adjoint sweep (Eqs. 56-57 without the Gauss-Newton
+  // drop): the derivative of the gradient's Heun-transposed recursion along the
+  // tangent trajectory.  Per step four evaluations of the ad~ / ad~^dagger
+  // bracket: G^T at v on (dU, dW) (the Gauss-Newton terms) and the same bracket
+  // with dv in place of v on the gradient sweep's (U, W) (the dropped terms:
+  // ad~^dagger_dv U, ad~^dagger_W dv - ad~_dv W), at the predictor and at the
+  // step's start.  Starts from (U, W) = (dU(1), 0); leaves dW(0) in W.
+  void newton_backward(State<T>& S) {
+    const double m = 1.0 / (double)Mvol;
+    if (!rec) cuda(cudaMemsetAsync(W, 0, (size_t)3 * Kvol * sizeof(C), st), "memset W");
+    if (persistent()) {
+      run_sweep(PW_GT, ev_newton, 4 * Nt);
+      return;
+    }
+    auto groups = [&](PiEpi<T>& e) {
+      e.grp[0] = 0; e.coef[0] = (T)m;  e.applyK[0] = 1;   // ad^dag_v U
+      e.grp[1] = 1; e.coef[1] = (T)m;  e.applyK[1] = 1;   // ad^dag_W v
+      e.grp[2] = 1; e.coef[2] = (T)-m; e.applyK[2] = 0;   // -ad_v W
+    };
+    for (int n = Nt - 1; n >= 0; --n) {
+      // predictor stage: a = G^T_{v*}(dz) + G'_{dv*}(z_{n+1})
+      PiEpi<T> e1 = epi(3, 3);
+      groups(e1);
+      add_out(e1, aU, 0, 1.0, {});
+      add_out(e1, aW, 1, 1.0, {{U, 1.0}});
+      eval(PW_GT, slot(S, 2 * n + 1), W, U, e1);
+      PiEpi<T> e2 = epi(3, 3);
+      groups(e2);
+      add_out(e2, aU, 0, 1.0, {{aU, 1.0}});
+      add_out(e2, aW, 1, 1.0, {{aW, 1.0}});
+      add_out(e2, Ut, 0, dt, {{U, 1.0}, {aU, dt}});
+      add_out(e2, Wt, 1, dt, {{W, 1.0}, {aW, dt}});
+      eval(PW_GT, tslot(2 * n + 1), vec(Wh, n + 1), vec(Uh, n + 1), e2);
+      // step start: b = G^T_{v_n}(dz~) + G'_{dv_n}(z~); dz_n = dz + dt/2 (a + b)
+      PiEpi<T> e3 = epi(3, 3);
+      groups(e3);
+      add_out(e3, bU, 0, 1.0, {});
+      add_out(e3, bW, 1, 1.0, {{Ut, 1.0}});
+      eval(PW_GT, slot(S, 2 * n), Wt, Ut, e3);
+      PiEpi<T> e4 = epi(3, 3);
+      groups(e4);
+      add_out(e4, U, 0, 0.5 * dt, {{U, 1.0}, {aU, 0.5 * dt}, {bU, 0.5 * dt}});
+      add_out(e4, W, 1, 0.5 * dt, {{W, 1.0}, {aW, 0.5 * dt}, {bW, 0.5 * dt}});
+      eval(PW_GT, tslot(2 * n), vec(Wth, n), vec(Uth, n), e4);
     }
   }
 
@@ -851,13 +958,14 @@ struct Impl {
     const double E = read_energy();
     have_lin = true;
     have_dm1 = false;
+    have_zhist = false;
     return E;
   }
 
   // enqueue one GN Hessian-vector product: input dvh[0], output vout
-  void enqueue_hessvec() {
+  void enqueue_hessvec(bool newton = false) {
     State<T>& S = lin;
-    tangent(S);
+    tangent(S, newton);
     if (!opts.recompute) {
       to_grid(dvh, Nt + 1, dvgrid);
     } else {                                  // regenerate step 0 of the state history
@@ -880,10 +988,16 @@ struct Impl {
       pe(PR_INC, 12.0 * (double)Nvol);
     }
     launches += Nt;
-    terminal_field<T>(m1(S), dm[Nt & 1], 0, -2.0 / (sigma * sigma), fterm, N, st);
+    if (newton)
+      terminal_newton<T>(m1(S), I1, dm[Nt & 1], -2.0 / (sigma * sigma), fterm, N, st);
+    else
+      terminal_field<T>(m1(S), dm[Nt & 1], 0, -2.0 / (sigma * sigma), fterm, N, st);
     ++launches;
     project_K(fterm, U);
-    backward(S);
+    if (newton)
+      newton_backward(S);
+    else
+      backward(S);
     axpby<T>(vout, 1.0, dvh, 1.0, W, 3 * Kvol, st);
     ++launches;
     check_launch("hessvec");
@@ -929,10 +1043,11 @@ struct Impl {
     energy_terms(lin);
     terminal_field<T>(m1(lin), I1, 1, -2.0 / (sigma * sigma), fterm, N, st);
     ++launches;
-    project_K(fterm, U);
-    backward(lin);
-    axpby<T>(gdev, 1.0, lin.vh, 1.0, W, 3 * Kvol, st);
+    project_K(fterm, vec(Uh, Nt));
+    backward_hist(lin);
+    axpby<T>(gdev, 1.0, lin.vh, 1.0, Wh, 3 * Kvol, st);
     ++launches;
+    have_zhist = true;
     check_launch("gradient");
     const double E = read_energy();
     have_lin = true;
@@ -961,6 +1076,10 @@ struct Impl {
   }
 
   void invalidate_graph() {
+    if (hv_exec_newton) {
+      cudaGraphExecDestroy(hv_exec_newton);
+      hv_exec_newton = nullptr;
+    }
     if (hv_exec) {
       cudaGraphExecDestroy(hv_exec);
       hv_exec = nullptr;
@@ -982,14 +1101,19 @@ struct Impl {
   }
 
   // Hessian-vector product with input already in dvh[0]; result in vout
-  void hessvec_dev() {
+  void hessvec_dev(bool newton = false) {
     if (!have_lin) {
       *err = "no linearisation point (call lddmm_gradient first)";
       throw Fail{LDDMM_ESTATE};
     }
-    if (opts.use_graphs && !hv_exec) {
+    if (newton && !have_zhist) {
+      *err = "the full-Newton product needs the backward sweep of lddmm_gradient at this point";
+      throw Fail{LDDMM_ESTATE};
+    }
+    cudaGraphExec_t& exec = newton ? hv_exec_newton : hv_exec;
+    if (opts.use_graphs && !exec) {
       try {
-        build_graph();
+        build_graph(newton);
       } catch (const Fail&) {
         // capture refused (e.g. a launch kind the graph cannot hold): run the
         // product with direct launches from now on
@@ -1001,18 +1125,18 @@ struct Impl {
     if (opts.use_graphs) {
       cuda(cudaEventRecord(ev, st), "event record");
       cuda(cudaStreamWaitEvent(cap, ev, 0), "wait");
-      cuda(cudaGraphLaunch(hv_exec, cap), "graph launch");
+      cuda(cudaGraphLaunch(exec, cap), "graph launch");
       graph_pending = !graph_pairs.empty();
       cuda(cudaEventRecord(ev, cap), "event record");
       cuda(cudaStreamWaitEvent(st, ev, 0), "wait");
-      launches += hv_nodes;
+      launches += newton ? hv_nodes_newton : hv_nodes;
     } else {
-      enqueue_hessvec();
+      enqueue_hessvec(newton);
     }
     have_dm1 = true;
   }
 
-  void build_graph() {
+  void build_graph(bool newton = false) {
     cudaStream_t user = st;
     st = cap;
     const long long before = launches;
@@ -1020,7 +1144,7 @@ struct Impl {
     cuda(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
     capturing = true;
     try {
-      enqueue_hessvec();
+      enqueue_hessvec(newton);
     } catch (...) {
       capturing = false;
       cudaStreamEndCapture(cap, &g);
@@ -1031,9 +1155,9 @@ struct Impl {
     capturing = false;
     st = user;
     cuda(cudaStreamEndCapture(cap, &g), "end capture");
-    hv_nodes = launches - before;
+    (newton ? hv_nodes_newton : hv_nodes) = launches - before;
     launches = before;
-    cudaError_t e = cudaGraphInstantiate(&hv_exec, g, 0);
+    cudaError_t e = cudaGraphInstantiate(newton ? &hv_exec_newton : &hv_exec, g, 0);
     cudaGraphDestroy(g);
     cuda(e, "graph instantiate");
   }
@@ -1045,6 +1169,19 @@ struct Impl {
     }
     load_bl(dv, dvh);
     hessvec_dev();
+    store_bl(vout, out);
+    cuda(cudaMemcpyAsync(hres + 7, dres + 7, sizeof(double), cudaMemcpyDeviceToHost, st), "read flag");
+    sync("hessvec");
+    check_flag(hres[7]);
+  }
+
+  void hessvec_newton(const void* dv, void* out) {
+    if (!have_lin) {
+      *err = "no linearisation point (call lddmm_gradient first)";
+      throw Fail{LDDMM_ESTATE};
+    }
+    load_bl(dv, dvh);
+    hessvec_dev(true);
     store_bl(vout, out);
     cuda(cudaMemcpyAsync(hres + 7, dres + 7, sizeof(double), cudaMemcpyDeviceToHost, st), "read flag");
     sync("hessvec");
@@ -1081,7 +1218,7 @@ struct Impl {
       int its = 0;
       for (int k = 1; k <= n_pcg; ++k) {
         cuda(cudaMemcpyAsync(dvh, pd, bytes, cudaMemcpyDeviceToDevice, st), "copy");
-        hessvec_dev();
+        hessvec_dev(opts.newton != 0);
         cuda(cudaMemcpyAsync(pq, vout, bytes, cudaMemcpyDeviceToDevice, st), "copy");
         const double dq = dot_V(pd, pq);
         if (!(dq > 0.0)) {
@@ -1248,6 +1385,7 @@ struct Impl {
     sync("transport vjp");
     check_flag(hres[7]);
     have_lin = true;
+    have_zhist = false;
     have_dm1 = false;
   }
 
@@ -1312,6 +1450,7 @@ void lddmm_default_opts(lddmm_opts* o) {
   o->tensor_cores = 1;
   o->recompute = 0;
   o->autotune = 1;
+  o->newton = 0;
 }
 
 int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, double alpha, int s,
@@ -1376,6 +1515,12 @@ int lddmm_gradient(lddmm_ctx* ctx, const void* v0, void* g, double* E) {
     const double e = im.gradient(v0, g);
     if (E) *E = e;
   });
+}
+
+int lddmm_hessvec_newton(lddmm_ctx* ctx, const void* dv, void* out) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, dv, "dv") || bad_ptr(ctx, out, "Hdv_out")) return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) { im.hessvec_newton(dv, out); });
 }
 
 int lddmm_exact_gradient(lddmm_ctx* ctx, const void* v0, void* g, double* E) {

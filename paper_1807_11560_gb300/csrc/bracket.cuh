@@ -244,8 +244,8 @@ __device__ __forceinline__ void phase_iota_ab(const Plan<T>& p, const FieldSpec<
 // up to 4), so C works on 4 planes and C' on 4 band slots per thread.
 template <typename T, int MODE>
 __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __restrict__ T2,
-                                          T* __restrict__ slot, cplx<T>* __restrict__ P2, int TP, int vb,
-                                          unsigned char* smraw) {
+                                          T* __restrict__ slot, T* __restrict__ slot2,
+                                          cplx<T>* __restrict__ P2, int TP, int vb, unsigned char* smraw) {
   using C = cplx<T>;
   constexpr int NP = (MODE == PW_GT) ? 9 : 3;
   const int G1 = p.g.n1, H1 = p.b.h1;
@@ -272,6 +272,8 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
   // tile-major, [tile][24][G1][TP] (the layout of sG), so these loads are
   // contiguous across the threads of a warp.
   T* __restrict__ tslot = slot + (long long)vb * 24 * G1 * TP;
+  // tangent sweeps may also cache the fields they transform (full-Newton products)
+  T* __restrict__ tslot2 = (MODE == PW_T && slot2 != nullptr) ? slot2 + (long long)vb * 24 * G1 * TP : nullptr;
   T cv[2][12], cl[2][12];
   if (MODE != PW_F) {
 #pragma unroll
@@ -323,6 +325,7 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
       if (x1 < G1) {
         sG[(f * G1 + x1) * TP + pp] = vv[t];
         if (MODE == PW_F) tslot[(f * G1 + x1) * TP + pp] = vv[t];
+        if (MODE == PW_T && tslot2 != nullptr) tslot2[(f * G1 + x1) * TP + pp] = vv[t];
       }
     }
   }

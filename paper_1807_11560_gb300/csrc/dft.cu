@@ -53,9 +53,10 @@ k_iota_AB(Plan<T> p, IotaDesc<T> d, const T* __restrict__ Lhat, cplx<T>* __restr
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads)
-k_cpw(Plan<T> p, const cplx<T>* __restrict__ T2, T* __restrict__ slot, cplx<T>* __restrict__ P2, int TP) {
+k_cpw(Plan<T> p, const cplx<T>* __restrict__ T2, T* __restrict__ slot, T* __restrict__ slot2,
+      cplx<T>* __restrict__ P2, int TP) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  dev::phase_cpw<T, MODE>(p, T2, slot, P2, TP, blockIdx.x, smraw);
+  dev::phase_cpw<T, MODE>(p, T2, slot, slot2, P2, TP, blockIdx.x, smraw);
 }
 
 template <typename T>
@@ -261,7 +262,8 @@ void bracket_iota(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>
 }
 
 template <typename T>
-void bracket_cpw(const Plan<T>& p, PwMode mode, const cplx<T>* T2, T* slot, cplx<T>* P2, cudaStream_t st) {
+void bracket_cpw(const Plan<T>& p, PwMode mode, const cplx<T>* T2, T* slot, T* slot2, cplx<T>* P2,
+                 cudaStream_t st) {
   const int TP = dev::cpw_tile(p);
   const int NP = (mode == PW_GT) ? 9 : 3;
   const size_t smem = dev::cpw_smem(p, TP, NP);
@@ -270,15 +272,15 @@ void bracket_cpw(const Plan<T>& p, PwMode mode, const cplx<T>* T2, T* slot, cplx
   switch (mode) {
     case PW_F:
       allow_smem<k_cpw<T, PW_F>>();
-      k_cpw<T, PW_F><<<grid, kThreads, smem, st>>>(p, T2, slot, P2, TP);
+      k_cpw<T, PW_F><<<grid, kThreads, smem, st>>>(p, T2, slot, slot2, P2, TP);
       break;
     case PW_T:
       allow_smem<k_cpw<T, PW_T>>();
-      k_cpw<T, PW_T><<<grid, kThreads, smem, st>>>(p, T2, slot, P2, TP);
+      k_cpw<T, PW_T><<<grid, kThreads, smem, st>>>(p, T2, slot, slot2, P2, TP);
       break;
     case PW_GT:
       allow_smem<k_cpw<T, PW_GT>>();
-      k_cpw<T, PW_GT><<<grid, kThreads, smem, st>>>(p, T2, slot, P2, TP);
+      k_cpw<T, PW_GT><<<grid, kThreads, smem, st>>>(p, T2, slot, slot2, P2, TP);
       break;
   }
 }
@@ -298,7 +300,7 @@ void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T
   template void pi_batch<T>(const Plan<T>&, const PiSrc<T>&, const PiEpi<T>&, const T*, cplx<T>*,  \
                             cudaStream_t);                                                         \
   template void bracket_iota<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t); \
-  template void bracket_cpw<T>(const Plan<T>&, PwMode, const cplx<T>*, T*, cplx<T>*, cudaStream_t); \
+  template void bracket_cpw<T>(const Plan<T>&, PwMode, const cplx<T>*, T*, T*, cplx<T>*, cudaStream_t); \
   template void bracket_pi<T>(const Plan<T>&, const PiEpi<T>&, const T*, const cplx<T>*, cudaStream_t);
 LDDMM_DFT_INST(float)
 LDDMM_DFT_INST(double)

@@ -233,6 +233,20 @@ k_adj_step(const T* __restrict__ lam, const T* __restrict__ m, const T* __restri
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
+k_terminal_newton(const T* __restrict__ m, const T* __restrict__ y, const T* __restrict__ dm, T c,
+                  T* __restrict__ out, Dims g) {
+  const long long vol = g.vol();
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= vol) return;
+  int ix[3];
+  unflat(idx, g.n2, g.n3, ix);
+  const T d = dm[idx], r = m[idx] - y[idx];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) out[j * vol + idx] = c * (d * cdiff(m, ix, j, g) + r * cdiff(dm, ix, j, g));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
 k_scaled_diff(const T* __restrict__ a, const T* __restrict__ b, T c, T* __restrict__ out, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = c * (a[i] - b[i]);
@@ -375,6 +389,11 @@ void adjoint_step(const T* lam, const T* m, const T* vcur, const T* vnext, const
 }
 
 template <typename T>
+void terminal_newton(const T* m, const T* y, const T* dm, double c, T* out, Dims g, cudaStream_t st) {
+  k_terminal_newton<T><<<blocks_for(g.vol()), kThreads, 0, st>>>(m, y, dm, (T)c, out, g);
+}
+
+template <typename T>
 void scaled_diff(const T* a, const T* b, double c, T* out, long long n, cudaStream_t st) {
   k_scaled_diff<T><<<blocks_for(n), kThreads, 0, st>>>(a, b, (T)c, out, n);
 }
@@ -423,6 +442,7 @@ void inner_V(const cplx<T>* a, const cplx<T>* b, const T* Lhat, int ncomp, long 
   template void adjoint_step<T>(const T*, const T*, const T*, const T*, const T*, T*, T*, T*, Dims,  \
                                 double, cudaStream_t);                                              \
   template void scaled_diff<T>(const T*, const T*, double, T*, long long, cudaStream_t);          \
+  template void terminal_newton<T>(const T*, const T*, const T*, double, T*, Dims, cudaStream_t);  \
   template void hermitianize<T>(const cplx<T>*, cplx<T>*, int, Band, cudaStream_t);             \
   template void axpby<T>(cplx<T>*, double, const cplx<T>*, double, const cplx<T>*, long long,    \
                          cudaStream_t);                                                          \

@@ -129,7 +129,7 @@ template <typename T>
 void bracket_iota(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2,
                   cudaStream_t st);
 template <typename T>
-void bracket_cpw(const Plan<T>& p, PwMode mode, const cplx<T>* T2, T* slot, cplx<T>* P2,
+void bracket_cpw(const Plan<T>& p, PwMode mode, const cplx<T>* T2, T* slot, T* slot2, cplx<T>* P2,
                  cudaStream_t st);
 template <typename T>
 void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T>* P2,
@@ -141,6 +141,7 @@ struct EvalDesc {
   const cplx<T>* srcA;
   const cplx<T>* srcB;
   T* slot;
+  T* slot2;      // tangent sweeps: where to cache the fields of A (nullptr: none)
   PiEpi<T> epi;
 };
 // Every evaluation of a band-limited sweep in one cooperative launch
@@ -198,6 +199,10 @@ void terminal_field(const T* m, const T* y, int diff, double coef, T* out, Dims 
 template <typename T>
 void adjoint_step(const T* lam, const T* m, const T* vcur, const T* vnext, const T* off, T* lam_out, T* gnext,
                   T* gcur, Dims g, double dt, cudaStream_t st);
+// out_j = c (dm d_j m + (m - y) d_j dm): the terminal field of the full-Newton
+// incremental adjoint (central differences)
+template <typename T>
+void terminal_newton(const T* m, const T* y, const T* dm, double c, T* out, Dims g, cudaStream_t st);
 // out = c (a - b)
 template <typename T>
 void scaled_diff(const T* a, const T* b, double c, T* out, long long n, cudaStream_t st);

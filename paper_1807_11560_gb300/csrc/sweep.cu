@@ -137,7 +137,7 @@ k_sweep(SweepArgs<T> a) {
     }
     if (!grid_barrier(a.bar, target, a.flag)) return;
     for (int vb = blockIdx.x; vb < n_cpw; vb += gridDim.x) {
-      dev::phase_cpw<T, MODE>(p, a.T2, slot, a.P2, a.TP, vb, smraw);
+      dev::phase_cpw<T, MODE>(p, a.T2, slot, E->slot2, a.P2, a.TP, vb, smraw);
       __syncthreads();
     }
     if (!grid_barrier(a.bar, target, a.flag)) return;

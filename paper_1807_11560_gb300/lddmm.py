@@ -32,7 +32,7 @@ class Opts(ctypes.Structure):
                 ("pcg_tol", ctypes.c_double), ("armijo_c", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("persistent", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("recompute", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("recompute", ctypes.c_int), ("autotune", ctypes.c_int), ("newton", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -107,6 +107,7 @@ def lib():
         "lddmm_gradient": (I, [P, P, P, ctypes.POINTER(D)]),
         "lddmm_hessvec": (I, [P, P, P]),
         "lddmm_exact_gradient": (I, [P, P, P, ctypes.POINTER(D)]),
+        "lddmm_hessvec_newton": (I, [P, P, P]),
         "lddmm_gn_solve": (I, [P, P, I, I, ctypes.POINTER(Report)]),
         "lddmm_batch_gn_solve": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P), I, I,
                                      ctypes.POINTER(Report), I]),
@@ -173,7 +174,7 @@ class Context:
 
     def __init__(self, grid, K, alpha, s, sigma, Nt, precision="fp32", stream=None,
                  use_graphs=True, pcg_tol=1e-12, armijo_c=1e-4, max_halvings=10, persistent="auto",
-                 tensor_cores="auto", recompute=False, autotune=True):
+                 tensor_cores="auto", recompute=False, autotune=True, newton=False):
         L = lib()
         self.grid, self.K = tuple(int(g) for g in grid), tuple(int(k) for k in K)
         self.ndim = len(self.grid)
@@ -189,6 +190,7 @@ class Context:
         o.tensor_cores = {True: 2, False: 0, "auto": 1}[tensor_cores]
         o.recompute = 1 if recompute else 0
         o.autotune = 1 if autotune else 0
+        o.newton = 1 if newton else 0
         o.pcg_tol, o.armijo_c, o.max_halvings = pcg_tol, armijo_c, max_halvings
         arr = ctypes.c_int * self.ndim
         h = ctypes.c_void_p()
@@ -252,6 +254,11 @@ class Context:
         self._check(lib().lddmm_gradient(self._h, self._arg(v0, "cplx", self.nband),
                                          self._arg(g_out, "cplx", self.nband), ctypes.byref(E)))
         return E.value
+
+    def hessvec_newton(self, dv, out):
+        """Full-Newton Hessian-vector product at the last gradient point."""
+        self._check(lib().lddmm_hessvec_newton(self._h, self._arg(dv, "cplx", self.nband),
+                                               self._arg(out, "cplx", self.nband)))
 
     def exact_gradient(self, v0, g_out):
         """V-gradient of the discretised energy (exact discrete adjoint); returns E."""
