@@ -91,6 +91,7 @@ struct Impl {
   T *dm[2] = {nullptr, nullptr}, *sb[2] = {nullptr, nullptr};
   T* fterm = nullptr;        // [3][Nvol]
   double *partial = nullptr, *dres = nullptr;   // dres[7]: sweep barrier time-out flag
+  double* dpcg = nullptr;    // [PCG_SLOTS] device conjugate-gradient scalars
   double* hres = nullptr;    // pinned host mirror of dres
   // persistent sweeps: evaluation descriptors recorded once at creation
   std::vector<EvalDesc<T>>* rec = nullptr;
@@ -375,6 +376,7 @@ struct Impl {
     alloc(fterm, (size_t)3 * Nvol);
     alloc(partial, (size_t)kReduceBlocks);
     alloc(dres, 8);
+    alloc(dpcg, PCG_SLOTS);
     cuda(cudaMemset(dres, 0, 8 * sizeof(double)), "memset");
     cuda(cudaMallocHost(&hres, 8 * sizeof(double)), "cudaMallocHost");
     if (opts.autotune && !persistent()) autotune();
@@ -1213,30 +1215,34 @@ struct Impl {
       axpby<T>(pr, -1.0, gbuf, 0.0, nullptr, 3 * Kvol, st);
       cuda(cudaMemcpyAsync(pd, pr, bytes, cudaMemcpyDeviceToDevice, st), "copy");
       ++launches;
-      double rho = dot_V(pr, pr);
-      const double bnorm = std::sqrt(rho);
-      int its = 0;
+      // the scalars stay on the device; the host looks at the stop flag every
+      // fourth iteration (iterations after a stop only repeat the product)
+      inner_V<T>(pr, pr, Lhat, 3, Kvol, partial, dpcg + PCG_R, st);
+      pcg_init(dpcg, st);
+      launches += 3;
+      const long long n3 = 3 * Kvol;
       for (int k = 1; k <= n_pcg; ++k) {
         cuda(cudaMemcpyAsync(dvh, pd, bytes, cudaMemcpyDeviceToDevice, st), "copy");
         hessvec_dev(opts.newton != 0);
         cuda(cudaMemcpyAsync(pq, vout, bytes, cudaMemcpyDeviceToDevice, st), "copy");
-        const double dq = dot_V(pd, pq);
-        if (!(dq > 0.0)) {
-          if (k == 1) cuda(cudaMemcpyAsync(px, pd, bytes, cudaMemcpyDeviceToDevice, st), "copy");
-          its = k - 1;
-          break;
+        inner_V<T>(pd, pq, Lhat, 3, Kvol, partial, dpcg + PCG_DQ, st);
+        pcg_alpha(dpcg, st);
+        copy_if<T>(px, pd, dpcg, n3, st);
+        axpy_dev<T>(px, px, pd, dpcg, PCG_A, 1.0, n3, st);
+        axpy_dev<T>(pr, pr, pq, dpcg, PCG_A, -1.0, n3, st);
+        inner_V<T>(pr, pr, Lhat, 3, Kvol, partial, dpcg + PCG_RN, st);
+        pcg_beta(dpcg, opts.pcg_tol, st);
+        axpy_dev<T>(pd, pr, pd, dpcg, PCG_BETA, 1.0, n3, st);
+        launches += 10;
+        if (k % 4 == 0 && k < n_pcg) {
+          cuda(cudaMemcpyAsync(hres, dpcg + PCG_DONE, sizeof(double), cudaMemcpyDeviceToHost, st), "read");
+          sync("pcg");
+          if (hres[0] != 0.0) break;
         }
-        const double a = rho / dq;
-        axpby<T>(px, 1.0, px, a, pd, 3 * Kvol, st);
-        axpby<T>(pr, 1.0, pr, -a, pq, 3 * Kvol, st);
-        launches += 2;
-        const double rho_new = dot_V(pr, pr);
-        its = k;
-        if (std::sqrt(rho_new) <= opts.pcg_tol * bnorm) break;
-        axpby<T>(pd, 1.0, pr, rho_new / rho, pd, 3 * Kvol, st);
-        ++launches;
-        rho = rho_new;
       }
+      cuda(cudaMemcpyAsync(hres, dpcg + PCG_ITS, sizeof(double), cudaMemcpyDeviceToHost, st), "read");
+      sync("pcg");
+      const int its = (int)hres[0];
       r.pcg_iters += its;
       if (r.pcg_hist) r.pcg_hist[it] = its;
       // Armijo backtracking along p (Eq. 44 with the step sign read as +)

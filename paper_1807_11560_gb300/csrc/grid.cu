@@ -289,6 +289,74 @@ __global__ void k_hermitianize(const cplx<T>* __restrict__ in, cplx<T>* __restri
   out[idx] = v;
 }
 
+// ---- conjugate gradients with device-resident scalars (Eq. 45) ------------------
+// s[] holds rho, ||b||, <d, Hd>, alpha, rho_new, beta, the stop flag, the
+// iterations done, the iteration counter and the "x = d" flag; every update
+// reads its coefficient here and does nothing once the stop flag is set, so the
+// host needs no round trip per iteration.
+__global__ void k_pcg_init(double* s) {
+  s[PCG_B] = sqrt(s[PCG_R]);
+  s[PCG_DONE] = 0.0;
+  s[PCG_ITS] = 0.0;
+  s[PCG_K] = 0.0;
+  s[PCG_COPY] = 0.0;
+}
+
+// after <d, Hd>: alpha = rho / <d, Hd>, or stop at non-positive curvature (the
+// first iteration then returns x = d, the steepest-descent direction)
+__global__ void k_pcg_alpha(double* s) {
+  const double k = s[PCG_K] + 1.0;
+  s[PCG_K] = k;
+  s[PCG_COPY] = 0.0;
+  if (s[PCG_DONE] != 0.0) {
+    s[PCG_A] = 0.0;
+    return;
+  }
+  const double dq = s[PCG_DQ];
+  if (!(dq > 0.0)) {
+    s[PCG_DONE] = 1.0;
+    s[PCG_ITS] = k - 1.0;
+    if (k == 1.0) s[PCG_COPY] = 1.0;
+    s[PCG_A] = 0.0;
+    return;
+  }
+  s[PCG_A] = s[PCG_R] / dq;
+}
+
+// after rho_new: stop on the relative residual, else beta = rho_new / rho
+__global__ void k_pcg_beta(double* s, double tol) {
+  if (s[PCG_DONE] != 0.0) return;
+  s[PCG_ITS] = s[PCG_K];
+  const double rn = s[PCG_RN];
+  if (sqrt(rn) <= tol * s[PCG_B]) {
+    s[PCG_DONE] = 1.0;
+    return;
+  }
+  s[PCG_BETA] = rn / s[PCG_R];
+  s[PCG_R] = rn;
+}
+
+// out = x + sign s[ci] y unless stopped
+template <typename T>
+__global__ void k_axpy_dev(cplx<T>* out, const cplx<T>* x, const cplx<T>* y, const double* s, int ci, double sign,
+                           long long n) {
+  if (s[PCG_DONE] != 0.0) return;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T b = (T)(sign * s[ci]);
+  cplx<T> v = x[i];
+  v.x = fma(b, y[i].x, v.x);
+  v.y = fma(b, y[i].y, v.y);
+  out[i] = v;
+}
+
+template <typename T>
+__global__ void k_copy_if(cplx<T>* out, const cplx<T>* in, const double* s, long long n) {
+  if (s[PCG_COPY] == 0.0) return;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[i];
+}
+
 template <typename T>
 __global__ void k_axpby(cplx<T>* out, T a, const cplx<T>* x, T bc, const cplx<T>* y, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -414,6 +482,21 @@ void axpby(cplx<T>* out, double a, const cplx<T>* x, double bcoef, const cplx<T>
   k_axpby<T><<<blocks_for(n), kThreads, 0, st>>>(out, (T)a, x, (T)bcoef, y, n);
 }
 
+void pcg_init(double* s, cudaStream_t st) { k_pcg_init<<<1, 1, 0, st>>>(s); }
+void pcg_alpha(double* s, cudaStream_t st) { k_pcg_alpha<<<1, 1, 0, st>>>(s); }
+void pcg_beta(double* s, double tol, cudaStream_t st) { k_pcg_beta<<<1, 1, 0, st>>>(s, tol); }
+
+template <typename T>
+void axpy_dev(cplx<T>* out, const cplx<T>* x, const cplx<T>* y, const double* s, int ci, double sign, long long n,
+              cudaStream_t st) {
+  k_axpy_dev<T><<<blocks_for(n), kThreads, 0, st>>>(out, x, y, s, ci, sign, n);
+}
+
+template <typename T>
+void copy_if(cplx<T>* out, const cplx<T>* in, const double* s, long long n, cudaStream_t st) {
+  k_copy_if<T><<<blocks_for(n), kThreads, 0, st>>>(out, in, s, n);
+}
+
 template <typename T>
 void scale_L(cplx<T>* out, const cplx<T>* x, const T* Lhat, int ncomp, long long kvol, cudaStream_t st) {
   k_scale_L<T><<<blocks_for(ncomp * kvol), kThreads, 0, st>>>(out, x, Lhat, kvol, ncomp * kvol);
@@ -447,6 +530,9 @@ void inner_V(const cplx<T>* a, const cplx<T>* b, const T* Lhat, int ncomp, long 
   template void axpby<T>(cplx<T>*, double, const cplx<T>*, double, const cplx<T>*, long long,    \
                          cudaStream_t);                                                          \
   template void scale_L<T>(cplx<T>*, const cplx<T>*, const T*, int, long long, cudaStream_t);    \
+  template void axpy_dev<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const double*, int, double,  \
+                            long long, cudaStream_t);                                              \
+  template void copy_if<T>(cplx<T>*, const cplx<T>*, const double*, long long, cudaStream_t);     \
   template void sum_sq_diff<T>(const T*, const T*, long long, double*, double*, cudaStream_t);   \
   template void inner_V<T>(const cplx<T>*, const cplx<T>*, const T*, int, long long, double*,    \
                            double*, cudaStream_t);

@@ -225,5 +225,16 @@ template <typename T>
 void inner_V(const cplx<T>* a, const cplx<T>* b, const T* Lhat, int ncomp, long long kvol,
              double* partial, double* out, cudaStream_t st);
 constexpr int kReduceBlocks = 304;   // 2 x 152 SMs
+// device-resident conjugate-gradient scalars (grid.cu)
+enum PcgSlot { PCG_R = 0, PCG_B, PCG_DQ, PCG_A, PCG_RN, PCG_BETA, PCG_DONE, PCG_ITS, PCG_K, PCG_COPY,
+               PCG_SLOTS = 16 };
+void pcg_init(double* s, cudaStream_t st);                 // ||b|| = sqrt(rho), counters reset
+void pcg_alpha(double* s, cudaStream_t st);                // alpha or the curvature stop
+void pcg_beta(double* s, double tol, cudaStream_t st);     // residual stop or beta
+template <typename T>                                      // out = x + sign s[ci] y unless stopped
+void axpy_dev(cplx<T>* out, const cplx<T>* x, const cplx<T>* y, const double* s, int ci, double sign, long long n,
+              cudaStream_t st);
+template <typename T>                                      // out = in if s[PCG_COPY]
+void copy_if(cplx<T>* out, const cplx<T>* in, const double* s, long long n, cudaStream_t st);
 
 }  // namespace lddmm
