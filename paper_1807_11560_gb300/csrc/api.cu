@@ -568,7 +568,7 @@ struct Impl {
       return;
     }
     pb(PR_IOTA_AB);
-    bracket_iota<T>(pad, block24(srcA, srcB, slot), Lhat, T2, st);
+    bracket_iota<T>(pad, block24(srcA, srcB, slot), Lhat, T2, st, use_tc_pad() ? dres + 7 : nullptr);
     pe(PR_IOTA_AB, flops_iota_ab());
     pb(PR_CPW);
     bracket_cpw<T>(pad, mode, T2, slot, slot2, P2, st);
@@ -596,6 +596,10 @@ struct Impl {
   bool use_tc() const {
     return opts.tensor_cores == 2 || (opts.tensor_cores == 1 && Nvol >= kTensorMinVoxels);
   }
+  // tensor-core iota A+B of the bracket evaluations (per-evaluation launches
+  // only): on request; at 160x192x160 / 32^3 it measures slower than the SIMT
+  // kernel (one 128-row work item per SM against four SIMT CTAs per SM)
+  bool use_tc_pad() const { return opts.tensor_cores == 2 && !persistent(); }
   bool persistent() const {
     if (rec != nullptr || opts.persistent == 0) return false;
     return opts.persistent == 2 || Mvol <= kPersistentMaxPadded;

@@ -257,7 +257,20 @@ void pi_batch(const Plan<T>& p, const PiSrc<T>& s, const PiEpi<T>& e, const T* L
 }
 
 template <typename T>
-void bracket_iota(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2, cudaStream_t st) {
+bool try_ab_tc(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, double*, cudaStream_t) {
+  return false;
+}
+template <>
+bool try_ab_tc<float>(const Plan<float>& p, const IotaDesc<float>& d, const float* Lhat, float2* T2,
+                      double* flag, cudaStream_t st) {
+  if (!flag || !iota_ab_tc_supported(p)) return false;
+  return iota_ab_tc(p, d, Lhat, T2, flag, st) == cudaSuccess;
+}
+
+template <typename T>
+void bracket_iota(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2, cudaStream_t st,
+                  double* tc_flag) {
+  if (try_ab_tc<T>(p, d, Lhat, T2, tc_flag, st)) return;
   launch_iota_AB<T>(p, d, Lhat, T2, st);
 }
 
@@ -299,7 +312,7 @@ void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T
                               double*);                                                            \
   template void pi_batch<T>(const Plan<T>&, const PiSrc<T>&, const PiEpi<T>&, const T*, cplx<T>*,  \
                             cudaStream_t);                                                         \
-  template void bracket_iota<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t); \
+  template void bracket_iota<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t, double*); \
   template void bracket_cpw<T>(const Plan<T>&, PwMode, const cplx<T>*, T*, T*, cplx<T>*, cudaStream_t); \
   template void bracket_pi<T>(const Plan<T>&, const PiEpi<T>&, const T*, const cplx<T>*, cudaStream_t);
 LDDMM_DFT_INST(float)

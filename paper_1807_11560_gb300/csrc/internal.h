@@ -106,6 +106,10 @@ void iota_batch(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* 
                 cudaStream_t st, double* tc_flag = nullptr);
 // tcgen05 image-grid stage C (tc_iota.cu)
 bool iota_C_tc_supported(const Plan<float>& p);
+// tcgen05 iota stages A + B of a padded-grid bracket block (tc_bracket.cu)
+bool iota_ab_tc_supported(const Plan<float>& p);
+cudaError_t iota_ab_tc(const Plan<float>& p, const IotaDesc<float>& d, const float* Lhat, float2* T2,
+                       double* flag, cudaStream_t st);
 cudaError_t iota_C_tc(const Plan<float>& p, const IotaDesc<float>& d, const float2* T2, double* flag,
                       cudaStream_t st);
 template <typename T>
@@ -126,8 +130,8 @@ enum PwMode { PW_F = 0, PW_T = 1, PW_GT = 2 };
 //                 (d's own fields) and read in PW_T and PW_GT;
 //   bracket_pi    pi stages B'+A' of P2 and the epilogue e.
 template <typename T>
-void bracket_iota(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2,
-                  cudaStream_t st);
+void bracket_iota(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2, cudaStream_t st,
+                  double* tc_flag = nullptr);
 template <typename T>
 void bracket_cpw(const Plan<T>& p, PwMode mode, const cplx<T>* T2, T* slot, T* slot2, cplx<T>* P2,
                  cudaStream_t st);

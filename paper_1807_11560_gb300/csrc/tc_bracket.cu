@@ -1,0 +1,330 @@
+// Tensor-core (tcgen05, sm_103a) form of iota stages A and B on the padded
+// product grid (the first phase of a bracket evaluation, Eqs. 46 and 48):
+// for a band slab (field f, h) with its spectral multiplier applied,
+//
+//   A   S1[k2][x3]  = sum_k3 S0[k2][k3] E3[k3][x3]
+//   B   T2[x2][x3]  = sum_k2 E2[k2][x2] S1[k2][x3]
+//
+// two complex GEMMs with inner dimensions K3 and K2.  In real form (re/im
+// interleaved along every dimension) each is a TN GEMM D = A B^T on tcgen05
+// with the 3xTF32 split of both operands:
+//   A: D_A[(s, k2)][(x3, c)] = sum_(k3, c') S0[(s, k2)][(k3, c')] E3x[(x3, c)][(k3, c')]
+//      M = S slabs x K2 rows (one 128-row tile), N = 2 G3, K = 2 K3;
+//   B: D_B[(s, x3)][(x2, c)] = sum_(k2, c') S1[(s, x3)][(k2, c')] E2x[(x2, c)][(k2, c')]
+//      M = S G3 rows in 128-row passes, N = 2 G2, K = 2 K2,
+// where E3x, E2x are the real forms of the twiddles ([[re, -im], [im, re]]
+// blocks), staged once per CTA.  D_A leaves TMEM (lane = (s, k2)) and is
+// written into the K-major A operand of stage B (row = (s, x3)), each lane
+// walking its x3 values in a lane-rotated order so the warp's shared-memory
+// writes spread over the banks.  D_B leaves TMEM with lane = (s, x3), so for
+// every x2 a warp stores 32 consecutive x3 of T2 (256 contiguous bytes).
+// Global loads are batched (eight per thread in flight).  One CTA per SM
+// (512 TMEM columns); every MMA wait is bounded.
+#include <algorithm>
+#include <cstdint>
+
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace lddmm {
+namespace {
+
+using namespace tc;
+
+constexpr int kThr = 256;
+constexpr long long kWait = 1LL << 24;
+
+struct AbTc {
+  int S;        // slabs per work item
+  int KA, KB;   // K of stages A and B (2 K3, 2 K2)
+  int NA, NB;   // N of stages A and B (2 G3, 2 G2, rounded up to 16)
+  int passes;   // 128-row passes of stage B
+};
+
+__device__ __forceinline__ int sfq(int q, int K) { return (2 * q < K) ? q : q - K; }
+__device__ __forceinline__ bool nyqq(int q, int K) { return (K % 2 == 0) && (2 * q == K); }
+
+// real form of a complex twiddle: row (x, c) of the output, column (k, c')
+__device__ __forceinline__ float twx(float2 e, int c, int cp) {
+  return c == 0 ? (cp == 0 ? e.x : -e.y) : (cp == 0 ? e.y : e.x);
+}
+
+__global__ void __launch_bounds__(kThr)
+k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, float2* __restrict__ T2, AbTc g,
+             double* flag) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  float* sm = reinterpret_cast<float*>(smraw);
+  const int R = kMTile * max(g.KA, g.KB);
+  float* Ahi = sm;                                  // A operand (stage A, then stage B)
+  float* Alo = sm + R;
+  float* BAhi = sm + 2 * R;                         // E3x
+  float* BAlo = BAhi + g.NA * g.KA;
+  float* BBhi = BAlo + g.NA * g.KA;                 // E2x
+  float* BBlo = BBhi + g.NB * g.KB;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(BBlo + g.NB * g.KB);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+  const int G2 = p.g.n2, G3 = p.g.n3, K2 = p.b.k2, K3 = p.b.k3, H1 = p.b.h1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nslab = d.nf * H1;
+  const int nitems = (nslab + g.S - 1) / g.S;
+
+  // twiddle operands, once per CTA: each complex twiddle fills a 2 x 2 block
+  // of its real form
+  auto stage_tw = [&](const float2* __restrict__ E, int Kc, int G, float* hi, float* lo, int Kx, int N) {
+    for (int base = 0; base < Kc * G; base += 8 * kThr) {
+      float2 e[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = base + u * kThr + tid;
+        e[u] = i < Kc * G ? E[i] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = base + u * kThr + tid;
+        if (i < Kc * G) {
+          const int k = i / G, x = i - k * G;
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int cp = 0; cp < 2; ++cp) {
+              const float v = twx(e[u], c, cp);
+              const float h = tf32_hi(v);
+              const int o = kmajor_off(2 * x + c, 2 * k + cp, Kx);
+              hi[o] = h;
+              lo[o] = v - h;
+            }
+        }
+      }
+    }
+    for (int i = tid; i < (N - 2 * G) * Kx; i += kThr) {   // zero rows of the N padding
+      const int o = kmajor_off(2 * G + i / Kx, i % Kx, Kx);
+      hi[o] = 0.f;
+      lo[o] = 0.f;
+    }
+  };
+  stage_tw(p.E3f, K3, G3, BAhi, BAlo, g.KA, g.NA);
+  stage_tw(p.E2f, K2, G2, BBhi, BBlo, g.KB, g.NB);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = *tslot;
+
+  const uint32_t idA = idesc_tf32(kMTile, g.NA), idB = idesc_tf32(kMTile, g.NB);
+  const uint32_t sboA = (uint32_t)(g.KA >> 2) * 128, sboB = (uint32_t)(g.KB >> 2) * 128;
+  uint32_t phase = 0;
+  bool ok = true;
+  // one 3xTF32 product tile: D (+)= Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T
+  auto issue = [&](uint32_t dcol, const float* ah, const float* al, const float* bh, const float* bl, int K,
+                   uint32_t sbo, uint32_t idesc) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    for (int s = 0; s < K / 8; ++s) {
+      const uint32_t so = (uint32_t)s * 256;
+      const uint64_t dah = smem_desc(smem_u32(ah) + so, 128, sbo);
+      const uint64_t dal = smem_desc(smem_u32(al) + so, 128, sbo);
+      const uint64_t dbh = smem_desc(smem_u32(bh) + so, 128, sbo);
+      const uint64_t dbl = smem_desc(smem_u32(bl) + so, 128, sbo);
+      mma_tf32(dcol, dah, dbh, idesc, s > 0 ? 1u : 0u);
+      mma_tf32(dcol, dah, dbl, idesc, 1u);
+      mma_tf32(dcol, dal, dbh, idesc, 1u);
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(mbar))
+                 : "memory");
+  };
+  // bounded wait for the last commit; every thread polls, all agree
+  auto wait = [&]() {
+    long long it = 0;
+    bool mine = true;
+    while (!mbar_try_wait(smem_u32(mbar), phase)) {
+      if (++it > kWait) {
+        mine = false;
+        break;
+      }
+    }
+    phase ^= 1u;
+    ok = __syncthreads_and(mine ? 1 : 0) != 0;
+    if (!ok && tid == 0) *(volatile double*)flag = 1.0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return ok;
+  };
+  const int q = warp & 3, half = warp >> 2;
+  const uint32_t tlane = (uint32_t)(32 * q) << 16;
+
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int sl0 = item * g.S;
+    // 1. stage A operand: the multiplied band slabs, rows (s, k2), K = (k3, c).
+    //    A warp takes 8 x 4 tiles (8 rows k2 x 4 columns k3): full 32-byte
+    //    sectors from global memory and at most 2-way bank conflicts in the
+    //    K-major layout; eight tiles' loads in flight per thread.
+    {
+      const int t2 = K2 / 8, t3 = K3 / 4, ntile = g.S * t2 * t3;
+      const int r8 = lane >> 2, c4 = lane & 3;
+      for (int base = warp; base < ntile; base += 8 * (kThr / 32)) {
+        float2 a[8];
+        float l[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int t = base + u * (kThr / 32);
+          a[u] = make_float2(0.f, 0.f);
+          l[u] = 1.f;
+          if (t < ntile) {
+            const int j = t / (t2 * t3), rem = t - j * (t2 * t3);
+            const int k2 = (rem / t3) * 8 + r8, k3 = (rem % t3) * 4 + c4;
+            const int sl = sl0 + j;
+            if (sl < nslab) {
+              const int f = sl / H1, h = sl - f * H1;
+              const long long off = ((long long)h * K2 + k2) * K3 + k3;
+              a[u] = d.src[f][off];
+              if (d.applyL[f]) l[u] = Lhat[off];
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int t = base + u * (kThr / 32);
+          if (t >= ntile) continue;
+          const int j = t / (t2 * t3), rem = t - j * (t2 * t3);
+          const int k2 = (rem / t3) * 8 + r8, k3 = (rem % t3) * 4 + c4;
+          const int sl = sl0 + j;
+          float2 v = make_float2(0.f, 0.f);
+          if (sl < nslab && !nyqq(k2, K2) && !nyqq(k3, K3)) {
+            const int f = sl / H1, h = sl - f * H1;
+            v = a[u];
+            v.x *= l[u];
+            v.y *= l[u];
+            const int dv = d.deriv[f];
+            if (dv >= 0) {
+              const float fr = dv == 0 ? (float)h : (dv == 1 ? (float)sfq(k2, K2) : (float)sfq(k3, K3));
+              const float w = (float)6.283185307179586476925286766559 * fr;
+              const float vx = -v.y * w;
+              v.y = v.x * w;
+              v.x = vx;
+            }
+          }
+          const float hr = tf32_hi(v.x), hm = tf32_hi(v.y);
+          const int o = kmajor_off(j * K2 + k2, 2 * k3, g.KA);
+          *reinterpret_cast<float2*>(Ahi + o) = make_float2(hr, hm);
+          *reinterpret_cast<float2*>(Alo + o) = make_float2(v.x - hr, v.y - hm);
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) issue(tbase, Ahi, Alo, BAhi, BAlo, g.KA, sboA, idA);
+    if (!wait()) break;
+    // 2. D_A -> stage B operand, 128 rows (s, x3) per pass
+    const int r = 32 * q + lane;                     // D_A row (s, k2)
+    const int js = r / K2, k2 = r - js * K2;
+    for (int ps = 0; ps < g.passes; ++ps) {
+      if (ps > 0 && !wait()) break;                  // the previous pass has read the operand
+      for (int c0 = 16 * half; c0 < g.NA; c0 += 32) {
+        float v[16];
+        tmem_ld16(tbase + tlane + (uint32_t)c0, v);
+        if (js < g.S) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int ii = (i + lane) & 7;
+            const int x3 = (c0 >> 1) + ii;
+            const int row = js * G3 + x3 - ps * kMTile;
+            if (x3 < G3 && row >= 0 && row < kMTile) {
+              const float re = v[2 * ii], im = v[2 * ii + 1];
+              const float hr = tf32_hi(re), hm = tf32_hi(im);
+              const int o = kmajor_off(row, 2 * k2, g.KB);
+              *reinterpret_cast<float2*>(Ahi + o) = make_float2(hr, hm);
+              *reinterpret_cast<float2*>(Alo + o) = make_float2(re - hr, im - hm);
+            }
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) issue(tbase + (uint32_t)(g.NA + ps * g.NB), Ahi, Alo, BBhi, BBlo, g.KB, sboB, idB);
+    }
+    if (!ok || !wait()) break;
+    // 3. D_B -> T2[f][h][x2][x3]
+    for (int ps = 0; ps < g.passes; ++ps) {
+      const int row = ps * kMTile + 32 * q + lane;    // (s, x3)
+      const int jj = row / G3, x3 = row - jj * G3;
+      const int sl = sl0 + jj;
+      const bool live = jj < g.S && sl < nslab;
+      float2* __restrict__ dst = T2 + (long long)(live ? sl : 0) * G2 * G3 + x3;
+      for (int c0 = 16 * half; c0 < g.NB; c0 += 32) {
+        float v[16];
+        tmem_ld16(tbase + tlane + (uint32_t)(g.NA + ps * g.NB + c0), v);
+        if (live) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int x2 = (c0 >> 1) + i;
+            if (x2 < G2) dst[(long long)x2 * G3] = make_float2(v[2 * i], v[2 * i + 1]);
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
+}
+
+int r16(int n) { return ((n + 15) / 16) * 16; }
+
+bool ab_tc_geom(const Plan<float>& p, AbTc& g, size_t& smem) {
+  const int K2 = p.b.k2, K3 = p.b.k3, G2 = p.g.n2, G3 = p.g.n3;
+  if (K2 % 8 != 0 || K3 % 4 != 0 || K2 > kMTile) return false;
+  g.KA = 2 * K3;
+  g.KB = 2 * K2;
+  g.NA = r16(2 * G3);
+  g.NB = r16(2 * G2);
+  if (g.NA > 256 || g.NB > 256) return false;
+  for (g.S = kMTile / K2; g.S >= 1; --g.S) {
+    g.passes = (g.S * G3 + kMTile - 1) / kMTile;
+    if (g.NA + g.passes * g.NB <= 512) break;
+  }
+  if (g.S < 1) return false;
+  smem = (size_t)(2 * kMTile * std::max(g.KA, g.KB) + 2 * g.NA * g.KA + 2 * g.NB * g.KB) * sizeof(float) + 16;
+  return smem <= 200 * 1024;
+}
+
+}  // namespace
+
+bool iota_ab_tc_supported(const Plan<float>& p) {
+  AbTc g;
+  size_t smem = 0;
+  return ab_tc_geom(p, g, smem);
+}
+
+cudaError_t iota_ab_tc(const Plan<float>& p, const IotaDesc<float>& d, const float* Lhat, float2* T2,
+                       double* flag, cudaStream_t st) {
+  AbTc g;
+  size_t smem = 0;
+  if (!ab_tc_geom(p, g, smem)) return cudaErrorInvalidValue;
+  // at least 140 KB: one CTA (and one 512-column TMEM allocation) per SM, and
+  // no room beside it for the image-grid kernel's TMEM either
+  smem = std::max<size_t>(smem, 140 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_iota_ab_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int nitems = (d.nf * p.b.h1 + g.S - 1) / g.S;
+  const unsigned grid = (unsigned)std::min(nitems, sms);
+  k_iota_ab_tc<<<grid, kThr, smem, st>>>(p, d, Lhat, T2, g, flag);
+  return cudaGetLastError();
+}
+
+}  // namespace lddmm

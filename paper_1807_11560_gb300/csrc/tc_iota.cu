@@ -28,75 +28,18 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace lddmm {
 namespace {
+
+using namespace tc;
 
 constexpr int kThreadsTC = 256;
 constexpr int kNT = 128;                 // grid pencils per work item
 constexpr int kMT = 128;                 // M tile (TMEM lanes = pencils)
 constexpr int kMaxKp = 48;               // K1 <= 48 (shared memory)
 constexpr long long kWaitLimit = 1LL << 24;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ float tf32_hi(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// float offset of element (row r, k) in a K-major no-swizzle operand tile with
-// Kp columns: core matrix (r/8, k/4) of 8 rows x 4 elements, rows 16 bytes apart
-__device__ __forceinline__ int kmajor_off(int r, int k, int Kp) {
-  return (((r >> 3) * (Kp >> 2) + (k >> 2)) << 5) + ((r & 7) << 2) + (k & 3);
-}
-
-// tcgen05 shared-memory descriptor: no swizzle, K-major; LBO = distance of
-// K-adjacent core matrices, SBO = distance of 8-row groups (bytes).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
 
 __global__ void __launch_bounds__(kThreadsTC)
 k_iota_C_tc(Plan<float> p, IotaDesc<float> d, const float2* __restrict__ T2, int Kp, int Np, double* flag) {
@@ -117,18 +60,31 @@ k_iota_C_tc(Plan<float> p, IotaDesc<float> d, const float2* __restrict__ T2, int
   const int tid = threadIdx.x, warp = tid >> 5;
   const int r = tid & (kNT - 1), h0 = tid >> 7;              // staging: pencil r, slots h0 + 2j
 
-  // B (both halves of the split) and the zero K padding of A, once per CTA
-  for (int idx = tid; idx < Np * Kp; idx += kThreadsTC) {
-    const int x1 = idx / Kp, k = idx - x1 * Kp;
-    float v = 0.f;
-    if (x1 < G1 && k < K) {
-      const float2 e = p.E1f[(k >> 1) * G1 + x1];
-      v = (k & 1) ? -e.y : e.x;
+  // B (both halves of the split) and the zero K padding of A, once per CTA;
+  // eight twiddle loads per thread in flight at a time
+  for (int base = 0; base < Np * Kp; base += 8 * kThreadsTC) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * kThreadsTC + tid;
+      const int x1 = idx / Kp, k = idx - x1 * Kp;
+      v[u] = 0.f;
+      if (idx < Np * Kp && x1 < G1 && k < K) {
+        const float2 e = p.E1f[(k >> 1) * G1 + x1];
+        v[u] = (k & 1) ? -e.y : e.x;
+      }
     }
-    const float hi = tf32_hi(v);
-    const int o = kmajor_off(x1, k, Kp);
-    Bhi[o] = hi;
-    Blo[o] = v - hi;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * kThreadsTC + tid;
+      if (idx < Np * Kp) {
+        const int x1 = idx / Kp, k = idx - x1 * Kp;
+        const float hi = tf32_hi(v[u]);
+        const int o = kmajor_off(x1, k, Kp);
+        Bhi[o] = hi;
+        Blo[o] = v[u] - hi;
+      }
+    }
   }
   for (int idx = tid; idx < kMT * (Kp - K); idx += kThreadsTC) {
     const int row = idx / (Kp - K), k = K + idx % (Kp - K);

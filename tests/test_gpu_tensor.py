@@ -45,3 +45,30 @@ def test_tensor_core_gradient_and_hessvec():
     assert abs(E - lin.E) / lin.E < 1e-6
     assert rel_V(host(g), lin.g, Ks) < 1e-5
     assert rel_V(host(Hp), P.hessvec(lin, p), Ks) < 1e-5
+
+
+@pytest.mark.parametrize("Ns,Ks", [((64, 64, 64), (32, 32, 32)), ((56, 48, 40), (24, 16, 24))])
+def test_tensor_core_bracket_iota_ab(Ns, Ks):
+    """tensor_cores=True also runs iota stages A+B of the padded-grid bracket
+    evaluations on tcgen05 (per-evaluation launches: persistent sweeps off):
+    gradient and Hessian-vector product against the FP64 oracle at 1e-5."""
+    import torch
+    Nt, seed = 2, 1812
+    I0, I1 = inputs.make_pair("brain", Ns, seed)
+    I0, I1 = quantise(I0, "fp32"), quantise(I1, "fp32")
+    v0 = quantise(inputs.random_bl(Ks, 3, seed + 1, 2.0, Ns), "fp32")
+    p = quantise(inputs.random_bl(Ks, 3, seed + 2, 1.0, Ns), "fp32")
+    ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision="fp32", tensor_cores=True, persistent=False)
+    ctx.set_images(torch_dev(I0, "fp32"), torch_dev(I1, "fp32"))
+    g = torch.empty((3,) + Ks, device="cuda", dtype=torch.complex64)
+    E = ctx.gradient(torch_dev(v0, "fp32"), g)
+    Hp = torch.empty_like(g)
+    ctx.hessvec(torch_dev(p, "fp32"), Hp)
+    g, Hp = host(g), host(Hp)
+    ctx.close()
+    from oracle import objective
+    P = objective.Problem(I0, I1, Ks, ALPHA, S, SIGMA, Nt)
+    lin = P.gradient(v0)
+    assert abs(E - lin.E) / lin.E < 1e-6
+    assert rel_V(g, lin.g, Ks) < 1e-5
+    assert rel_V(Hp, P.hessvec(lin, p), Ks) < 1e-5
