@@ -87,12 +87,13 @@ typedef struct {
                            (grid barriers with bounded waits): 0 never (three kernels per
                            bracket evaluation), 1 when the padded product grid has at
                            most 32^3 points (default), 2 always */
-  int tensor_cores;     /* FP32 contexts: band-to-image-grid transforms (iota stage C) on
-                           the tcgen05 tensor cores with the 3xTF32 split: 0 never,
-                           1 for image grids of at least 2^20 voxels (default), 2 always,
-                           and then also iota stages A+B of the padded-grid bracket
-                           evaluations launched per evaluation (where K2 is a multiple
-                           of 8, K3 of 4 and the tiles fit) */
+  int tensor_cores;     /* FP32 contexts, tcgen05 tensor cores with the 3xTF32 split for
+                           the band-to-grid transforms: iota stage C on the image grid
+                           and iota stages A+B of the bracket evaluations launched per
+                           evaluation (padded grids above 32^3 points, K2 a multiple of
+                           8, K3 of 4, tiles that fit).  0 never; 1 (default) for image
+                           grids of at least 2^20 voxels and those padded grids; 2
+                           whenever supported */
   int recompute;        /* image-grid histories of the time sweeps (velocity grids v_n,
                            characteristic displacements, states m_n, incremental
                            velocity grids): 0 keep all Nt + 1 steps (default); 1 keep

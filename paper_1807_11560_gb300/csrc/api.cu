@@ -23,6 +23,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/lddmm.h"
@@ -379,6 +380,15 @@ struct Impl {
     alloc(dpcg, PCG_SLOTS);
     cuda(cudaMemset(dres, 0, 8 * sizeof(double)), "memset");
     cuda(cudaMallocHost(&hres, 8 * sizeof(double)), "cudaMallocHost");
+    if constexpr (std::is_same<T, float>::value) {
+      // the tcgen05 iota A+B twiddle operands, expanded once (on request)
+      if (opts.tensor_cores != 0 && iota_ab_tc_supported(pad)) {
+        float* tw = nullptr;
+        alloc(tw, iota_ab_tc_twiddle_floats(pad));
+        cuda(iota_ab_tc_twiddles(pad, tw, st), "tensor-core twiddles");
+        pad.tc_ab = tw;
+      }
+    }
     if (opts.autotune && !persistent()) autotune();
     make_state(lin);                       // the cache layout follows the tile shapes
     make_state(trial);
@@ -596,10 +606,12 @@ struct Impl {
   bool use_tc() const {
     return opts.tensor_cores == 2 || (opts.tensor_cores == 1 && Nvol >= kTensorMinVoxels);
   }
-  // tensor-core iota A+B of the bracket evaluations (per-evaluation launches
-  // only): on request; at 160x192x160 / 32^3 it measures slower than the SIMT
-  // kernel (one 128-row work item per SM against four SIMT CTAs per SM)
-  bool use_tc_pad() const { return opts.tensor_cores == 2 && !persistent(); }
+  // tensor-core iota A+B of the bracket evaluations: the per-evaluation
+  // launches of padded grids above the persistent-sweep size
+  bool use_tc_pad() const {
+    return !persistent() &&
+           (opts.tensor_cores == 2 || (opts.tensor_cores == 1 && Mvol > kPersistentMaxPadded));
+  }
   bool persistent() const {
     if (rec != nullptr || opts.persistent == 0) return false;
     return opts.persistent == 2 || Mvol <= kPersistentMaxPadded;

@@ -52,6 +52,9 @@ struct Plan {
   // memory (iota A+B); tp = pencils per tile (C/products/C'); kc = band rows
   // per item (pi B'/A')
   int tws = 0, tp = 0, kc = 0;
+  // FP32 padded plans: the tcgen05 iota A+B twiddle operands, expanded once
+  // into the kernel's shared-memory layout (nullptr: expanded in the kernel)
+  const float* tc_ab = nullptr;
 };
 
 // iota batch: field f is iota of (multiplier x one scalar band slab), where
@@ -108,6 +111,9 @@ void iota_batch(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* 
 bool iota_C_tc_supported(const Plan<float>& p);
 // tcgen05 iota stages A + B of a padded-grid bracket block (tc_bracket.cu)
 bool iota_ab_tc_supported(const Plan<float>& p);
+// floats of the expanded twiddle operands, and the expansion into dst (device)
+size_t iota_ab_tc_twiddle_floats(const Plan<float>& p);
+cudaError_t iota_ab_tc_twiddles(const Plan<float>& p, float* dst, cudaStream_t st);
 cudaError_t iota_ab_tc(const Plan<float>& p, const IotaDesc<float>& d, const float* Lhat, float2* T2,
                        double* flag, cudaStream_t st);
 cudaError_t iota_C_tc(const Plan<float>& p, const IotaDesc<float>& d, const float2* T2, double* flag,

@@ -18,8 +18,10 @@
 // walking its x3 values in a lane-rotated order so the warp's shared-memory
 // writes spread over the banks.  D_B leaves TMEM with lane = (s, x3), so for
 // every x2 a warp stores 32 consecutive x3 of T2 (256 contiguous bytes).
-// Global loads are batched (eight per thread in flight).  One CTA per SM
-// (512 TMEM columns); every MMA wait is bounded.
+// Global loads are batched (eight per thread in flight); the twiddle operands
+// are expanded once per context and copied into each CTA; the common padded
+// sizes are compile-time constants.  One CTA of 512 threads per SM (512 TMEM
+// columns); every MMA wait is bounded.
 #include <algorithm>
 #include <cstdint>
 
@@ -31,7 +33,8 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThr = 256;
+constexpr int kThr = 512;
+constexpr int kWarps = kThr / 32;
 constexpr long long kWait = 1LL << 24;
 
 struct AbTc {
@@ -45,15 +48,51 @@ __device__ __forceinline__ int sfq(int q, int K) { return (2 * q < K) ? q : q - 
 __device__ __forceinline__ bool nyqq(int q, int K) { return (K % 2 == 0) && (2 * q == K); }
 
 // real form of a complex twiddle: row (x, c) of the output, column (k, c')
-__device__ __forceinline__ float twx(float2 e, int c, int cp) {
+__host__ __device__ __forceinline__ float twx(float2 e, int c, int cp) {
   return c == 0 ? (cp == 0 ? e.x : -e.y) : (cp == 0 ? e.y : e.x);
 }
 
+__host__ __device__ constexpr int r16d(int n) { return ((n + 15) / 16) * 16; }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(src) : "memory");
+}
+
+// the expanded twiddle operands [E3x hi | E3x lo | E2x hi | E2x lo], each in
+// the K-major layout of its shared-memory tile, one element per thread
+__global__ void k_ab_tc_twiddles(Plan<float> p, float* dst, int NA, int KA, int NB, int KB) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nA = (long long)NA * KA, nB = (long long)NB * KB;
+  if (i >= nA + nB) return;
+  const bool isA = i < nA;
+  const int Kx = isA ? KA : KB;
+  const int e = (int)(isA ? i : i - nA);
+  const int n = e / Kx, k = e - n * Kx;
+  const int G = isA ? p.g.n3 : p.g.n2;
+  const float2* E = isA ? p.E3f : p.E2f;
+  const float v = (n >> 1) < G ? twx(E[(k >> 1) * G + (n >> 1)], n & 1, k & 1) : 0.f;
+  const float h = tf32_hi(v);
+  float* base = isA ? dst : dst + 2 * nA;
+  const int o = kmajor_off(n, k, Kx);
+  base[o] = h;
+  base[(isA ? nA : nB) + o] = v - h;
+}
+
+// sizes known at compile time for the common padded grids (0: read at run time),
+// so the index arithmetic of the staging loops folds to constants
+template <int K2c, int K3c, int G2c, int G3c>
 __global__ void __launch_bounds__(kThr)
 k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, float2* __restrict__ T2, AbTc g,
              double* flag) {
   extern __shared__ __align__(128) unsigned char smraw[];
   float* sm = reinterpret_cast<float*>(smraw);
+  const int G2 = G2c ? G2c : p.g.n2, G3 = G3c ? G3c : p.g.n3, K2 = K2c ? K2c : p.b.k2, K3 = K3c ? K3c : p.b.k3;
+  const int H1 = p.b.h1;
+  g.KA = 2 * K3;
+  g.KB = 2 * K2;
+  g.NA = r16d(2 * G3);
+  g.NB = r16d(2 * G2);
   const int R = kMTile * max(g.KA, g.KB);
   float* Ahi = sm;                                  // A operand (stage A, then stage B)
   float* Alo = sm + R;
@@ -64,7 +103,6 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
   uint64_t* mbar = reinterpret_cast<uint64_t*>(BBlo + g.NB * g.KB);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
-  const int G2 = p.g.n2, G3 = p.g.n3, K2 = p.b.k2, K3 = p.b.k3, H1 = p.b.h1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nslab = d.nf * H1;
   const int nitems = (nslab + g.S - 1) / g.S;
@@ -103,8 +141,16 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
       lo[o] = 0.f;
     }
   };
-  stage_tw(p.E3f, K3, G3, BAhi, BAlo, g.KA, g.NA);
-  stage_tw(p.E2f, K2, G2, BBhi, BBlo, g.KB, g.NB);
+  if (p.tc_ab != nullptr) {                         // expanded once per context: copy
+    const int n4 = (2 * g.NA * g.KA + 2 * g.NB * g.KB) / 4;
+    const float4* src = reinterpret_cast<const float4*>(p.tc_ab);
+    float4* dst = reinterpret_cast<float4*>(BAhi);
+    for (int i = tid; i < n4; i += kThr) cp_async16(dst + i, src + i);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  } else {
+    stage_tw(p.E3f, K3, G3, BAhi, BAlo, g.KA, g.NA);
+    stage_tw(p.E2f, K2, G2, BBhi, BBlo, g.KB, g.NB);
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot))
                  : "memory");
@@ -157,7 +203,7 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     return ok;
   };
-  const int q = warp & 3, half = warp >> 2;
+  const int q = warp & 3, cg = warp >> 2;          // lane quadrant, column group (of 4)
   const uint32_t tlane = (uint32_t)(32 * q) << 16;
 
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
@@ -169,12 +215,12 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
     {
       const int t2 = K2 / 8, t3 = K3 / 4, ntile = g.S * t2 * t3;
       const int r8 = lane >> 2, c4 = lane & 3;
-      for (int base = warp; base < ntile; base += 8 * (kThr / 32)) {
+      for (int base = warp; base < ntile; base += 8 * kWarps) {
         float2 a[8];
         float l[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const int t = base + u * (kThr / 32);
+          const int t = base + u * kWarps;
           a[u] = make_float2(0.f, 0.f);
           l[u] = 1.f;
           if (t < ntile) {
@@ -191,7 +237,7 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const int t = base + u * (kThr / 32);
+          const int t = base + u * kWarps;
           if (t >= ntile) continue;
           const int j = t / (t2 * t3), rem = t - j * (t2 * t3);
           const int k2 = (rem / t3) * 8 + r8, k3 = (rem % t3) * 4 + c4;
@@ -227,7 +273,7 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
     const int js = r / K2, k2 = r - js * K2;
     for (int ps = 0; ps < g.passes; ++ps) {
       if (ps > 0 && !wait()) break;                  // the previous pass has read the operand
-      for (int c0 = 16 * half; c0 < g.NA; c0 += 32) {
+      for (int c0 = 16 * cg; c0 < g.NA; c0 += 64) {
         float v[16];
         tmem_ld16(tbase + tlane + (uint32_t)c0, v);
         if (js < g.S) {
@@ -237,7 +283,13 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
             const int x3 = (c0 >> 1) + ii;
             const int row = js * G3 + x3 - ps * kMTile;
             if (x3 < G3 && row >= 0 && row < kMTile) {
-              const float re = v[2 * ii], im = v[2 * ii + 1];
+              float re = 0.f, im = 0.f;                 // v[2 ii], v[2 ii + 1] from registers
+#pragma unroll
+              for (int m = 0; m < 8; ++m)
+                if (m == ii) {
+                  re = v[2 * m];
+                  im = v[2 * m + 1];
+                }
               const float hr = tf32_hi(re), hm = tf32_hi(im);
               const int o = kmajor_off(row, 2 * k2, g.KB);
               *reinterpret_cast<float2*>(Ahi + o) = make_float2(hr, hm);
@@ -259,7 +311,7 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
       const int sl = sl0 + jj;
       const bool live = jj < g.S && sl < nslab;
       float2* __restrict__ dst = T2 + (long long)(live ? sl : 0) * G2 * G3 + x3;
-      for (int c0 = 16 * half; c0 < g.NB; c0 += 32) {
+      for (int c0 = 16 * cg; c0 < g.NB; c0 += 64) {
         float v[16];
         tmem_ld16(tbase + tlane + (uint32_t)(g.NA + ps * g.NB + c0), v);
         if (live) {
@@ -308,6 +360,37 @@ bool iota_ab_tc_supported(const Plan<float>& p) {
   return ab_tc_geom(p, g, smem);
 }
 
+size_t iota_ab_tc_twiddle_floats(const Plan<float>& p) {
+  AbTc g;
+  size_t smem = 0;
+  if (!ab_tc_geom(p, g, smem)) return 0;
+  return (size_t)2 * g.NA * g.KA + (size_t)2 * g.NB * g.KB;
+}
+
+cudaError_t iota_ab_tc_twiddles(const Plan<float>& p, float* dst, cudaStream_t st) {
+  AbTc g;
+  size_t smem = 0;
+  if (!ab_tc_geom(p, g, smem)) return cudaErrorInvalidValue;
+  const long long n = (long long)g.NA * g.KA + (long long)g.NB * g.KB;
+  k_ab_tc_twiddles<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, dst, g.NA, g.KA, g.NB, g.KB);
+  return cudaGetLastError();
+}
+
+template <int K2c, int K3c, int G2c, int G3c>
+cudaError_t launch_ab_tc(const Plan<float>& p, const IotaDesc<float>& d, const float* Lhat, float2* T2,
+                         const AbTc& g, size_t smem, double* flag, cudaStream_t st) {
+  auto kern = k_iota_ab_tc<K2c, K3c, G2c, G3c>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int nitems = (d.nf * p.b.h1 + g.S - 1) / g.S;
+  const unsigned grid = (unsigned)std::min(nitems, sms);
+  kern<<<grid, kThr, smem, st>>>(p, d, Lhat, T2, g, flag);
+  return cudaGetLastError();
+}
+
 cudaError_t iota_ab_tc(const Plan<float>& p, const IotaDesc<float>& d, const float* Lhat, float2* T2,
                        double* flag, cudaStream_t st) {
   AbTc g;
@@ -316,15 +399,12 @@ cudaError_t iota_ab_tc(const Plan<float>& p, const IotaDesc<float>& d, const flo
   // at least 140 KB: one CTA (and one 512-column TMEM allocation) per SM, and
   // no room beside it for the image-grid kernel's TMEM either
   smem = std::max<size_t>(smem, 140 * 1024);
-  cudaError_t e = cudaFuncSetAttribute(k_iota_ab_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  const int nitems = (d.nf * p.b.h1 + g.S - 1) / g.S;
-  const unsigned grid = (unsigned)std::min(nitems, sms);
-  k_iota_ab_tc<<<grid, kThr, smem, st>>>(p, d, Lhat, T2, g, flag);
-  return cudaGetLastError();
+  const int K2 = p.b.k2, K3 = p.b.k3, G2 = p.g.n2, G3 = p.g.n3;
+  if (K2 == 32 && K3 == 32 && G2 == 48 && G3 == 48)
+    return launch_ab_tc<32, 32, 48, 48>(p, d, Lhat, T2, g, smem, flag, st);
+  if (K2 == 24 && K3 == 24 && G2 == 36 && G3 == 36)
+    return launch_ab_tc<24, 24, 36, 36>(p, d, Lhat, T2, g, smem, flag, st);
+  return launch_ab_tc<0, 0, 0, 0>(p, d, Lhat, T2, g, smem, flag, st);
 }
 
 }  // namespace lddmm
