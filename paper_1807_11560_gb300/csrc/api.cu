@@ -204,6 +204,29 @@ struct Impl {
     up(p.E1b, e1b);
     up(p.E2b, e2b);
     up(p.E3b, e3b);
+    // the same tables in the padded / transposed tile layouts of the phases
+    int G3e = 0, G2e = 0, G1q = 0, H1q = 0, G3s = 0;
+    staged_twiddle_dims<T>(p, &G3e, &G2e, &G1q, &H1q, &G3s);
+    const C zero{T(0), T(0)};
+    std::vector<C> e3fp((size_t)K.k3 * G3e, zero), e2fp((size_t)K.k2 * G2e, zero),
+        e1fp((size_t)H1 * G1q, zero), e1bp((size_t)g.n1 * H1q, zero), e3bt((size_t)K.k3 * G3s, zero);
+    for (int k = 0; k < K.k3; ++k)
+      for (int x = 0; x < g.n3; ++x) {
+        e3fp[(size_t)k * G3e + x] = e3f[(size_t)k * g.n3 + x];
+        e3bt[(size_t)k * G3s + x] = e3b[(size_t)x * K.k3 + k];
+      }
+    for (int k = 0; k < K.k2; ++k)
+      for (int x = 0; x < g.n2; ++x) e2fp[(size_t)k * G2e + x] = e2f[(size_t)k * g.n2 + x];
+    for (int h = 0; h < H1; ++h)
+      for (int x = 0; x < g.n1; ++x) {
+        e1fp[(size_t)h * G1q + x] = e1f[(size_t)h * g.n1 + x];
+        e1bp[(size_t)x * H1q + h] = e1b[(size_t)x * H1 + h];
+      }
+    up(p.E3fp, e3fp);
+    up(p.E2fp, e2fp);
+    up(p.E1fp, e1fp);
+    up(p.E1bp, e1bp);
+    up(p.E3bt, e3bt);
   }
 
   void make_state(State<T>& S) {

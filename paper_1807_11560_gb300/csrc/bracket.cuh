@@ -152,7 +152,10 @@ __device__ __forceinline__ void phase_iota_ab(const Plan<T>& p, const FieldSpec<
   T* sL = reinterpret_cast<T*>(TWS ? E2s + K2 * G2e : E3s);   // [K2][K3]
   const int tid = threadIdx.x;
   const C zero{T(0), T(0)};
-  if (TWS) {
+  if (TWS && p.E3fp != nullptr) {
+    cp_async_run(E3s, p.E3fp, K3 * G3e);
+    cp_async_run(E2s, p.E2fp, K2 * G2e);
+  } else if (TWS) {
     for (int i = tid; i < K3 * G3e; i += kThreads) {
       const int r = i / G3e, x = i - r * G3e;
       if (x < G3) cp_async(E3s + i, p.E3f + r * G3 + x); else E3s[i] = zero;
@@ -289,13 +292,18 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
       }
     }
   }
-  for (int i = tid; i < H1 * G1q; i += kThreads) {
-    const int h = i / G1q, x = i - h * G1q;
-    if (x < G1) cp_async(sE1f + i, p.E1f + h * G1 + x); else sE1f[i] = zero;
-  }
-  for (int i = tid; i < G1 * H1q; i += kThreads) {
-    const int x = i / H1q, h = i - x * H1q;
-    if (h < H1) cp_async(sE1b + i, p.E1b + x * H1 + h); else sE1b[i] = zero;
+  if (p.E1fp != nullptr) {
+    cp_async_run(sE1f, p.E1fp, H1 * G1q);
+    cp_async_run(sE1b, p.E1bp, G1 * H1q);
+  } else {
+    for (int i = tid; i < H1 * G1q; i += kThreads) {
+      const int h = i / G1q, x = i - h * G1q;
+      if (x < G1) cp_async(sE1f + i, p.E1f + h * G1 + x); else sE1f[i] = zero;
+    }
+    for (int i = tid; i < G1 * H1q; i += kThreads) {
+      const int x = i / H1q, h = i - x * H1q;
+      if (h < H1) cp_async(sE1b + i, p.E1b + x * H1 + h); else sE1b[i] = zero;
+    }
   }
   cp_async_wait_all();
   __syncthreads();
@@ -444,9 +452,13 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
     const int x2 = i / KC, kk = i - x2 * KC;
     if (kk < kc) cp_async(E2s + i, p.E2b + (long long)x2 * K2 + kb + kk); else E2s[i] = zero;
   }
-  for (int i = tid; i < G3 * K3; i += kThreads) {
-    const int x = i / K3, k = i - x * K3;
-    cp_async(E3s + k * G3s + x, p.E3b + i);
+  if (p.E3bt != nullptr) {
+    cp_async_run(E3s, p.E3bt, K3 * G3s);
+  } else {
+    for (int i = tid; i < G3 * K3; i += kThreads) {
+      const int x = i / K3, k = i - x * K3;
+      cp_async(E3s + k * G3s + x, p.E3b + i);
+    }
   }
   for (int i = tid; i < nslot * kEpiX; i += kThreads) {
     const int jq = i / nslot, it = i - jq * nslot;

@@ -201,6 +201,15 @@ bool tile_valid(const Plan<T>& p, int tws, int tp, int kc) {
 }
 
 template <typename T>
+void staged_twiddle_dims(const Plan<T>& p, int* G3e, int* G2e, int* G1q, int* H1q, int* G3s) {
+  *G3e = dev::even_up(p.g.n3);
+  *G2e = dev::even_up(p.g.n2);
+  *G1q = dev::quad_up(p.g.n1);
+  *H1q = dev::quad_up(p.b.h1);
+  *G3s = dev::e3_stride<T>(p.g.n3);
+}
+
+template <typename T>
 long long cache_slot_elems(const Plan<T>& p) {
   const long long P = (long long)p.g.n2 * p.g.n3;
   const int TP = dev::cpw_tile(p);
@@ -306,6 +315,7 @@ void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T
 #define LDDMM_DFT_INST(T)                                                                          \
   template size_t max_smem_needed<T>(const Plan<T>&, int, bool);                                   \
   template long long cache_slot_elems<T>(const Plan<T>&);                                           \
+  template void staged_twiddle_dims<T>(const Plan<T>&, int*, int*, int*, int*, int*);               \
   template void tile_config<T>(const Plan<T>&, int*, int*, int*);                                   \
   template bool tile_valid<T>(const Plan<T>&, int, int, int);                                        \
   template void iota_batch<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t,    \

@@ -55,6 +55,14 @@ struct Plan {
   // FP32 padded plans: the tcgen05 iota A+B twiddle operands, expanded once
   // into the kernel's shared-memory layout (nullptr: expanded in the kernel)
   const float* tc_ab = nullptr;
+  // the twiddle tiles exactly as the phase bodies stage them in shared memory
+  // (zero padded / transposed), so a phase copies them contiguously; nullptr:
+  // the phases build the tiles from the tables above
+  cplx<T>* E3fp = nullptr;   // [K3][G3e]  iota A (E3f, rows padded to even length)
+  cplx<T>* E2fp = nullptr;   // [K2][G2e]  iota B (E2f, padded to even length)
+  cplx<T>* E1fp = nullptr;   // [H1][G1q]  iota C (E1f, padded to a multiple of 4)
+  cplx<T>* E1bp = nullptr;   // [G1][H1q]  pi C' (E1b, padded to a multiple of 4)
+  cplx<T>* E3bt = nullptr;   // [K3][G3s]  pi A' (E3b transposed, bank-spread row stride)
 };
 
 // iota batch: field f is iota of (multiplier x one scalar band slab), where
@@ -176,6 +184,9 @@ size_t smem_limit();
 // [tile][24][M1][TP] so that a tile's fields are one contiguous block
 template <typename T>
 long long cache_slot_elems(const Plan<T>& p);
+// row lengths of the staged twiddle tiles: G3e, G2e, G1q, H1q, G3s
+template <typename T>
+void staged_twiddle_dims(const Plan<T>& p, int* G3e, int* G2e, int* G1q, int* H1q, int* G3s);
 // tile shapes in effect for a padded-grid plan (overrides or size heuristics):
 // twiddle staging of iota A+B (1 off, 2 on), pencils per tile of the
 // C/products/C' phase, band rows per pi B'/A' item (for 3 product fields)
