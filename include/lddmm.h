@@ -204,7 +204,10 @@ int lddmm_hessvec(lddmm_ctx* ctx, const void* dv, void* Hdv_out);
  * (early stop on ||r||_V <= pcg_tol ||b||_V or non-positive curvature),
  * Armijo backtracking v0 <- v0 + eps p.  v0_inout is read and overwritten.
  * rep may be NULL.  Stops early, with rep->ls_failed = 1, when a line search
- * accepts no step. */
+ * accepts no step.  The trial sweeps of the line search reuse the state of
+ * the linearisation (the accepted one becomes the next iteration's forward
+ * sweep), so on return there is no linearisation point: call lddmm_gradient
+ * before lddmm_hessvec. */
 int lddmm_gn_solve(lddmm_ctx* ctx, void* v0_inout, int n_gn, int n_pcg, lddmm_report* rep);
 
 /* Batched population: lddmm_gn_solve on n independent contexts at once (one

@@ -1082,6 +1082,12 @@ struct Impl {
          "copy v0");
     forward(lin);
     energy_terms(lin);
+    return gradient_tail(gdev);
+  }
+
+  // the rest of the gradient once lin holds the forward sweep of the point and
+  // dres[0..1] its energy terms
+  double gradient_tail(C* gdev) {
     terminal_field<T>(m1(lin), I1, 1, -2.0 / (sigma * sigma), fterm, N, st);
     ++launches;
     project_K(fterm, vec(Uh, Nt));
@@ -1240,8 +1246,15 @@ struct Impl {
     }
     const double c = opts.armijo_c;
     const size_t bytes = (size_t)3 * Kvol * sizeof(C);
+    // after PCG the linearisation is no longer needed in this iteration, so the
+    // line search's trial sweeps run in lin: the accepted trial's forward sweep
+    // and energy terms are then those of the next iterate, whose gradient
+    // continues from them
+    bool lin_at_vsol = false;
+    double E_last = 0.0;
     for (int it = 0; it < n_gn; ++it) {
-      const double E = gradient_dev(vsol, gbuf);
+      const double E = lin_at_vsol ? gradient_tail(gbuf) : gradient_dev(vsol, gbuf);
+      E_last = E;
       const double gn = std::sqrt(dot_V(gbuf, gbuf));
       if (it == 0) {
         r.E_initial = E;
@@ -1288,12 +1301,18 @@ struct Impl {
       const double slope = dot_V(gbuf, px);
       double eps = 1.0;
       bool ok = false;
+      have_lin = have_zhist = have_dm1 = false;
+      lin_at_vsol = false;
       for (int h = 0; h <= opts.max_halvings; ++h) {
         axpby<T>(vtry, 1.0, vsol, eps, px, 3 * Kvol, st);
         ++launches;
-        const double Et = energy_dev(vtry);
+        cuda(cudaMemcpyAsync(lin.vh, vtry, bytes, cudaMemcpyDeviceToDevice, st), "copy trial");
+        forward(lin);
+        energy_terms(lin);
+        const double Et = read_energy();
         if (Et <= E + c * eps * slope) {
           ok = true;
+          E_last = Et;
           break;
         }
         eps *= 0.5;
@@ -1305,9 +1324,11 @@ struct Impl {
       }
       if (r.eps_hist) r.eps_hist[it] = eps;
       cuda(cudaMemcpyAsync(vsol, vtry, bytes, cudaMemcpyDeviceToDevice, st), "copy");
+      lin_at_vsol = true;
       r.gn_iters = it + 1;
     }
-    r.E_final = energy_dev(vsol);
+    // the energy of the returned iterate is already known unless no iteration ran
+    r.E_final = n_gn > 0 ? E_last : energy_dev(vsol);
     store_bl(vsol, v0);
     sync("gn_solve");
     if (rep) *rep = r;
