@@ -24,6 +24,10 @@ objective  energy (Eq. 50), V-gradient (Eqs. 53-55), Gauss-Newton
            Hessian-vector product (Eqs. 30-31, 56-58 under the GN reading),
            the J-form diagnostic, PCG in the V inner product and the
            Gauss-Newton-Krylov outer loop with Armijo backtracking (Eqs. 44-45).
+deformation  the deformation-state form of Section 3.3: the band-limited
+           inverse-map displacement swept jointly with the shoot, its tangent,
+           the terminal image I0(x + u(1)), U~(1) = K~(D~phi~(1)^T * rho~(1)) and
+           the energy, gradient and GN product built on them.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 identities, brute-force sums and convergence orders.  Parity status: pinned
