@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--workload", default="3d_64_ellipsoids")
     ap.add_argument("--probe", default="auto", help="kernel class timed for the roofline (auto: dominant)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--state", default="image", choices=["image", "deformation"],
+                    help="constraint: image state equation (Section 3.2) or band-limited deformation "
+                         "state equation (Section 3.3)")
     ap.add_argument("--tensor-cores", default="auto", choices=["auto", "on", "off"],
                     help="image-grid band-to-grid transforms on tcgen05 (3xTF32): auto = grids >= 2^20 voxels")
     return ap.parse_args()
@@ -124,14 +127,15 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------- oracle
-def oracle_hessvec_rate(name, n_hv, seed_offset=0):
+def oracle_hessvec_rate(name, n_hv, seed_offset=0, state="image"):
     """Hessian-vector products of the FP64 oracle per second (bounded sample)."""
     import numpy as np
-    from oracle import objective
+    from oracle import deformation, objective
     from paper_1807_11560_gb300 import inputs
     kind, Ns, Ks, Nt, seed = workload(name)
     I0, I1 = inputs.make_pair(kind, Ns, seed + seed_offset)
-    P = objective.Problem(I0, I1, Ks, ALPHA, S, SIGMA, Nt)
+    cls = deformation.DeformationProblem if state == "deformation" else objective.Problem
+    P = cls(I0, I1, Ks, ALPHA, S, SIGMA, Nt)
     v0 = inputs.random_bl(Ks, len(Ns), seed + 1, 2.0, Ns)
     lin = P.gradient(v0)
     p = inputs.random_bl(Ks, len(Ns), seed + 2, 1.0, Ns)
@@ -149,7 +153,7 @@ def run_reference(args):
         return
     name = args.workload
     kind, Ns, Ks, Nt, seed = workload(name)
-    times = oracle_hessvec_rate(name, args.warmup + args.steps)[args.warmup:]
+    times = oracle_hessvec_rate(name, args.warmup + args.steps, state=args.state)[args.warmup:]
     total = sum(times)
     value = len(times) / total
     sample = (f"{len(times)} GN Hessian-vector products of the FP64 NumPy oracle at a fixed "
@@ -160,7 +164,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": name, "grid": list(Ns), "band": list(Ks), "Nt": Nt, "gn_iters": N_GN_CONFIG,
-                   "pcg_per_gn": N_PCG, "l2": "oracle on host cores",
+                   "pcg_per_gn": N_PCG, "state": args.state, "l2": "oracle on host cores",
                    "step": "one bounded sample: GN Hessian-vector products at a fixed linearisation point"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                          "host_cores": os.cpu_count()},
@@ -214,7 +218,7 @@ def measured_traffic(workload_name, cls):
     return None if entry is None else float(entry["bytes"])
 
 
-PROBE_CLASSES = ("sweep", "iota_ab", "cpw", "pi_ba", "inc_step", "transport", "iota_full", "pi_full")
+PROBE_CLASSES = ("sweep", "iota_ab", "cpw", "pi_ba", "inc_step", "transport", "iota_full", "pi_full", "deform")
 HBM_CLASSES = ("inc_step", "transport")
 SMS, FP32_LANES = 152, 128
 
@@ -253,7 +257,7 @@ def run_gpu(args):
     I0d = torch.as_tensor(I0, dtype=torch.float32, device=dev)
     I1d = torch.as_tensor(I1, dtype=torch.float32, device=dev)
     ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision="fp32",
-                  tensor_cores={"auto": "auto", "on": True, "off": False}[args.tensor_cores])
+                  tensor_cores={"auto": "auto", "on": True, "off": False}[args.tensor_cores], state=args.state)
     ctx.set_images(I0d, I1d)
     v = torch.zeros((d,) + tuple(Ks), dtype=torch.complex64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -376,7 +380,7 @@ def run_gpu(args):
             roof["class_ms_one_gn_iteration"] = class_ms
         cpu = None
         if not args.no_cpu_baseline:
-            times = oracle_hessvec_rate(name, 3)
+            times = oracle_hessvec_rate(name, 3, state=args.state)
             cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"{len(times)} GN Hessian-vector products of the FP64 NumPy oracle on {name} "
                              "at a fixed linearisation point (single-threaded numpy/pocketfft)",
@@ -387,7 +391,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": name, "grid": list(Ns), "band": list(Ks), "Nt": Nt,
-                       "gn_iters": N_GN_CONFIG, "pcg_per_gn": N_PCG,
+                       "gn_iters": N_GN_CONFIG, "pcg_per_gn": N_PCG, "state": args.state,
                        "step": f"one GN-Krylov solve from v0 = 0: {N_GN_CONFIG} GN iterations (gradient, "
                                f"{N_PCG} PCG Hessvecs, Armijo)",
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",

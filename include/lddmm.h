@@ -113,6 +113,15 @@ typedef struct {
   int newton;           /* Hessian used by lddmm_gn_solve's PCG: 0 Gauss-Newton (default),
                            1 full Newton (lddmm_hessvec_newton); PCG stops at the first
                            direction of non-positive curvature either way. */
+  int state_eq;         /* constraint of the registration problem: 0 the image state
+                           equation of Section 3.2 (default: m(t) transported on the
+                           image grid); 1 the deformation state equation of Section 3.3
+                           (the inverse map x + u(t)(x) carried as a band-limited
+                           displacement u~(t), m(1) = I0(x + u(1)(x))).  With 1,
+                           lddmm_energy, lddmm_gradient, lddmm_hessvec, lddmm_gn_solve,
+                           lddmm_batch_gn_solve and lddmm_transport follow Section 3.3;
+                           lddmm_exact_gradient, lddmm_hessvec_newton, lddmm_transport_vjp
+                           and newton = 1 are state-form only (LDDMM_EINVAL). */
 } lddmm_opts;
 
 /* Report of lddmm_gn_solve.  The per-iteration arrays are optional

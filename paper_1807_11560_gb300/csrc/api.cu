@@ -45,9 +45,9 @@ struct Fail {
 };
 
 enum ProbeClass { PR_TRANSPORT = 0, PR_INC, PR_IOTA_AB, PR_CPW, PR_PI_BA, PR_IOTA_FULL, PR_PI_FULL,
-                  PR_SWEEP, PR_COUNT };
+                  PR_SWEEP, PR_DEFORM, PR_COUNT };
 const char* const kProbeNames[PR_COUNT] = {"transport", "inc_step", "iota_ab", "cpw", "pi_ba",
-                                           "iota_full", "pi_full", "sweep"};
+                                           "iota_full", "pi_full", "sweep", "deform"};
 
 template <typename T>
 struct State {
@@ -57,6 +57,9 @@ struct State {
   T* vgrid = nullptr;       // [Nt+1][3][Nvol]  (recompute: [2][3][Nvol], step n in n & 1)
   T* mh = nullptr;          // [Nt+1][Nvol]     (recompute: [2][Nvol])
   T* off = nullptr;         // [Nt][3][Nvol]    (recompute: [3][Nvol], the current step)
+  // deformation-state form (Section 3.3): band-limited inverse-map displacement
+  cplx<T>* uh = nullptr;    // [Nt+1][3][Kvol]
+  cplx<T>* ush = nullptr;   // [Nt][3][Kvol]    Heun predictors u*_n
 };
 
 template <typename T>
@@ -108,6 +111,11 @@ struct Impl {
   cudaGraphExec_t hv_exec = nullptr, hv_exec_newton = nullptr;
   long long hv_nodes = 0, hv_nodes_newton = 0;
   bool have_zhist = false;   // Uh/Wh/Uth/Wth hold the last gradient's backward sweep
+  // deformation-state form (Section 3.3)
+  T* gI0 = nullptr;           // [3][Nvol] central-difference gradient of I0
+  T* defM = nullptr;          // [24][Mvol] padded-grid fields of the deformation products
+  T* prodM = nullptr;         // [3][Mvol] their products
+  C *dk1 = nullptr, *rhob = nullptr, *dua = nullptr, *dub = nullptr, *dup = nullptr;   // [3][Kvol]
   cudaStream_t cap = nullptr;
   cudaEvent_t ev = nullptr;
   bool capturing = false;
@@ -237,6 +245,10 @@ struct Impl {
     alloc(S.vgrid, steps * 3 * Nvol);
     alloc(S.mh, steps * Nvol);
     alloc(S.off, (opts.recompute ? 1 : (size_t)Nt) * 3 * Nvol);
+    if (deform()) {
+      alloc(S.uh, (size_t)(Nt + 1) * 3 * Kvol);
+      alloc(S.ush, (size_t)Nt * 3 * Kvol);
+    }
   }
   // ------------------------------------------------------------ autotuner
   // Times the candidate tile shapes of the three padded-grid bracket kernels
@@ -398,6 +410,12 @@ struct Impl {
       alloc(sb[i], (size_t)Nvol);
     }
     alloc(fterm, (size_t)3 * Nvol);
+    if (deform()) {
+      alloc(gI0, (size_t)3 * Nvol);
+      alloc(defM, (size_t)24 * Mvol);
+      alloc(prodM, (size_t)3 * Mvol);
+      for (C** b : {&dk1, &rhob, &dua, &dub, &dup}) alloc(*b, (size_t)3 * Kvol);
+    }
     alloc(partial, (size_t)kReduceBlocks);
     alloc(dres, 8);
     alloc(dpcg, PCG_SLOTS);
@@ -635,6 +653,12 @@ struct Impl {
     return !persistent() &&
            (opts.tensor_cores == 2 || (opts.tensor_cores == 1 && Mvol > kPersistentMaxPadded));
   }
+  bool deform() const { return opts.state_eq == 1; }
+  void state_form_only(const char* what) {
+    if (!deform()) return;
+    *err = std::string(what) + " is defined for the image state form only (opts.state_eq = 0)";
+    throw Fail{LDDMM_EINVAL};
+  }
   bool persistent() const {
     if (rec != nullptr || opts.persistent == 0) return false;
     return opts.persistent == 2 || Mvol <= kPersistentMaxPadded;
@@ -669,15 +693,15 @@ struct Impl {
     check_launch("iota to image grid");
   }
 
-  // K~ pi of a 3-component image-grid field -> band vector out
-  void project_K(const T* f3, C* out) {
+  // K~ pi (or pi alone) of a 3-component image-grid field -> band vector out
+  void project_K(const T* f3, C* out, bool applyK = true) {
     PiSrc<T> ps{};
     ps.nf = 3;
     for (int c = 0; c < 3; ++c) ps.src[c] = f3 + c * Nvol;
     PiEpi<T> e = epi(3, 1);
     e.grp[0] = 0;
     e.coef[0] = (T)(1.0 / (double)Nvol);
-    e.applyK[0] = 1;
+    e.applyK[0] = applyK ? 1 : 0;
     add_out(e, out, 0, 1.0, {});
     pb(PR_PI_FULL);
     pi_batch<T>(full, ps, e, Lhat, T2, st);
@@ -763,7 +787,115 @@ struct Impl {
 
   void forward(State<T>& S) {
     shoot(S);
+    if (deform()) {
+      deform_sweep(S);
+      deform_sample(S);
+      return;
+    }
     transport(S);
+  }
+
+  // ------------------------------------- deformation-state form (Section 3.3)
+  // Jacobian (d_j a_i in block 3 i + j) of band vector a and values of b onto
+  // the padded grid: iota fields base .. base + 11
+  void jac_val(IotaDesc<T>& d, int base, const C* a, const C* b) {
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        const int f = base + 3 * i + j;
+        d.src[f] = a + (long long)i * Kvol;
+        d.deriv[f] = (signed char)j;
+        d.applyL[f] = 0;
+      }
+    for (int c = 0; c < 3; ++c) {
+      const int f = base + 9 + c;
+      d.src[f] = b + (long long)c * Kvol;
+      d.deriv[f] = -1;
+      d.applyL[f] = 0;
+    }
+  }
+  // algorithmic flops of iota (or pi) of nf scalar fields on grid g
+  double grid_flops(const Dims& g, int nf) const {
+    const double H1 = K.h1, K2 = K.k2, K3 = K.k3;
+    return nf * (8.0 * H1 * (K2 * K3 * g.n3 + K2 * (double)g.n2 * g.n3) + 4.0 * H1 * (double)g.vol());
+  }
+  // one padded-grid product of the deformation form (def_products mode) with
+  // its iota fields {D a, b} (and {D a2, b2} for mode 1) and pi epilogue e
+  void def_eval(int mode, const C* a, const C* b, const C* a2, const C* b2, const PiEpi<T>& e) {
+    IotaDesc<T> d{};
+    d.nf = mode == 1 ? 24 : 12;
+    jac_val(d, 0, a, b);
+    if (mode == 1) jac_val(d, 12, a2, b2);
+    for (int f = 0; f < d.nf; ++f) d.dst[f] = defM + (long long)f * Mvol;
+    PiSrc<T> ps{};
+    ps.nf = 3;
+    for (int c = 0; c < 3; ++c) ps.src[c] = prodM + (long long)c * Mvol;
+    pb(PR_DEFORM);
+    iota_batch<T>(pad, d, Lhat, T2, st, nullptr);
+    def_products<T>(mode, defM, prodM, Mvol, st);
+    pi_batch<T>(pad, ps, e, Lhat, T2, st);
+    pe(PR_DEFORM, grid_flops(M, d.nf + 3) + (mode == 1 ? 42.0 : 21.0) * (double)Mvol);
+    launches += kIotaLaunches + 1 + kPiLaunches;
+    check_launch("deformation product");
+  }
+  PiEpi<T> def_epi(bool applyK) const {
+    PiEpi<T> e = epi(3, 1);
+    e.grp[0] = 0;
+    e.coef[0] = (T)(1.0 / (double)Mvol);
+    e.applyK[0] = applyK ? 1 : 0;
+    return e;
+  }
+
+  // Heun sweep of d/dt u~ = -v~ - D~u~ * v~ jointly with the shoot (stage 2 at
+  // the EPDiff predictor v*_n), u~(0) = 0
+  void deform_sweep(State<T>& S) {
+    cuda(cudaMemsetAsync(S.uh, 0, (size_t)3 * Kvol * sizeof(C), st), "memset u0");
+    for (int n = 0; n < Nt; ++n) {
+      C* un = vec(S.uh, n);
+      C* us = vec(S.ush, n);
+      PiEpi<T> e1 = def_epi(false);
+      add_out(e1, dk1, 0, 1.0, {});
+      add_out(e1, us, 0, dt, {{un, 1.0}});
+      def_eval(0, un, vec(S.vh, n), nullptr, nullptr, e1);
+      PiEpi<T> e2 = def_epi(false);
+      add_out(e2, vec(S.uh, n + 1), 0, 0.5 * dt, {{un, 1.0}, {dk1, 0.5 * dt}});
+      def_eval(0, us, vec(S.vsh, n), nullptr, nullptr, e2);
+    }
+  }
+
+  // m(1) = I0(x + u(1)(x)) into m1(S) and (grad I0)(x + u(1)(x)) into the first
+  // three fields of S.vgrid (u(1) on the grid goes to the next three)
+  void deform_sample(State<T>& S) {
+    T* u1 = S.vgrid + 3 * Nvol;
+    to_grid(vec(S.uh, Nt), 1, u1);
+    def_sample<T>(I0, gI0, u1, m1(S), S.vgrid, N, st);
+    ++launches;
+    check_launch("deformation terminal sampling");
+  }
+
+  // exact tangent of the deformation sweep along the shoot tangent (dvh, dvsh);
+  // returns the buffer holding delta u~(1)
+  C* deform_tangent(State<T>& S) {
+    C* cur = dua;
+    C* nxt = dub;
+    cuda(cudaMemsetAsync(cur, 0, (size_t)3 * Kvol * sizeof(C), st), "memset du0");
+    for (int n = 0; n < Nt; ++n) {
+      PiEpi<T> e1 = def_epi(false);
+      add_out(e1, dk1, 0, 1.0, {});
+      add_out(e1, dup, 0, dt, {{cur, 1.0}});
+      def_eval(1, cur, vec(S.vh, n), vec(S.uh, n), vec(dvh, n), e1);
+      PiEpi<T> e2 = def_epi(false);
+      add_out(e2, nxt, 0, 0.5 * dt, {{cur, 1.0}, {dk1, 0.5 * dt}});
+      def_eval(1, dup, vec(S.vsh, n), vec(S.ush, n), vec(dvsh, n), e2);
+      std::swap(cur, nxt);
+    }
+    return cur;
+  }
+
+  // U~(1) = K~ pi[r + (D u)^T r] on the padded grid, r = iota(r~), u = u~(1)
+  void terminal_deform(const C* r, const C* u, C* out) {
+    PiEpi<T> e = def_epi(true);
+    add_out(e, out, 0, 1.0, {});
+    def_eval(2, u, r, nullptr, nullptr, e);
   }
 
   // energy pieces into dres[0] (<v0,v0>_V) and dres[1] (sum (m1 - I1)^2)
@@ -1006,6 +1138,20 @@ struct Impl {
   // enqueue one GN Hessian-vector product: input dvh[0], output vout
   void enqueue_hessvec(bool newton = false) {
     State<T>& S = lin;
+    if (deform()) {                           // Section 3.3 under Gauss-Newton
+      tangent(S);
+      const C* du1 = deform_tangent(S);
+      to_grid(du1, 1, dvgrid);
+      def_force<T>(S.vgrid, m1(S), I1, dvgrid, dm[Nt & 1], -2.0 / (sigma * sigma), fterm, Nvol, st);
+      ++launches;
+      project_K(fterm, rhob, false);
+      terminal_deform(rhob, vec(S.uh, Nt), U);
+      backward(S);
+      axpby<T>(vout, 1.0, dvh, 1.0, W, 3 * Kvol, st);
+      ++launches;
+      check_launch("hessvec");
+      return;
+    }
     tangent(S, newton);
     if (!opts.recompute) {
       to_grid(dvh, Nt + 1, dvgrid);
@@ -1055,6 +1201,11 @@ struct Impl {
   void set_images(const void* a, const void* b) {
     cuda(cudaMemcpyAsync(I0, a, (size_t)Nvol * sizeof(T), cudaMemcpyDefault, st), "copy I0");
     cuda(cudaMemcpyAsync(I1, b, (size_t)Nvol * sizeof(T), cudaMemcpyDefault, st), "copy I1");
+    if (deform()) {
+      central_grad<T>(I0, gI0, N, st);
+      ++launches;
+      check_launch("gradient of I0");
+    }
     sync("set_images");
     have_images = true;
     have_lin = false;
@@ -1088,9 +1239,16 @@ struct Impl {
   // the rest of the gradient once lin holds the forward sweep of the point and
   // dres[0..1] its energy terms
   double gradient_tail(C* gdev) {
-    terminal_field<T>(m1(lin), I1, 1, -2.0 / (sigma * sigma), fterm, N, st);
-    ++launches;
-    project_K(fterm, vec(Uh, Nt));
+    if (deform()) {                           // U~(1) of Section 3.3
+      def_force<T>(lin.vgrid, m1(lin), I1, nullptr, nullptr, -2.0 / (sigma * sigma), fterm, Nvol, st);
+      ++launches;
+      project_K(fterm, rhob, false);
+      terminal_deform(rhob, vec(lin.uh, Nt), vec(Uh, Nt));
+    } else {
+      terminal_field<T>(m1(lin), I1, 1, -2.0 / (sigma * sigma), fterm, N, st);
+      ++launches;
+      project_K(fterm, vec(Uh, Nt));
+    }
     backward_hist(lin);
     axpby<T>(gdev, 1.0, lin.vh, 1.0, Wh, 3 * Kvol, st);
     ++launches;
@@ -1115,6 +1273,7 @@ struct Impl {
   }
 
   double exact_gradient(const void* v0, void* g) {
+    state_form_only("lddmm_exact_gradient");
     load_bl(v0, vsol);
     const double E = exact_gradient_dev(vsol, gbuf);
     store_bl(gbuf, g);
@@ -1223,6 +1382,7 @@ struct Impl {
   }
 
   void hessvec_newton(const void* dv, void* out) {
+    state_form_only("lddmm_hessvec_newton");
     if (!have_lin) {
       *err = "no linearisation point (call lddmm_gradient first)";
       throw Fail{LDDMM_ESTATE};
@@ -1432,6 +1592,7 @@ struct Impl {
 
   // l2 gradient of a loss of m(1) with respect to v0 (adjoint Jacobi sweep)
   void transport_vjp(const void* v0, const void* gm1, void* out) {
+    state_form_only("lddmm_transport_vjp");
     need_images();
     load_bl(v0, vsol);
     cuda(cudaMemcpyAsync(lin.vh, vsol, (size_t)3 * Kvol * sizeof(C), cudaMemcpyDeviceToDevice, st),
@@ -1517,6 +1678,7 @@ void lddmm_default_opts(lddmm_opts* o) {
   o->recompute = 0;
   o->autotune = 1;
   o->newton = 0;
+  o->state_eq = 0;
 }
 
 int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, double alpha, int s,
@@ -1536,6 +1698,8 @@ int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, doubl
   lddmm_default_opts(&o);
   if (opts) o = *opts;
   if (o.precision != LDDMM_FP32 && o.precision != LDDMM_FP64) return LDDMM_EINVAL;
+  if (o.state_eq != 0 && o.state_eq != 1) return LDDMM_EINVAL;
+  if (o.state_eq == 1 && o.newton != 0) return LDDMM_EINVAL;
   lddmm_ctx* ctx = new (std::nothrow) lddmm_ctx();
   if (!ctx) return LDDMM_ENOMEM;
   ctx->precision = o.precision;

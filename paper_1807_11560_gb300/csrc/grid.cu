@@ -2,7 +2,10 @@
 //   * semi-Lagrangian state and incremental-state transport on the image grid
 //     (Eqs. 52 and 31),
 //   * terminal adjoint fields lambda(1) grad m(1) (Eq. 55, Eq. 58 under GN),
-//   * band-vector updates and deterministic FP64 reductions (Eq. 47, Eq. 50).
+//   * band-vector updates and deterministic FP64 reductions (Eq. 47, Eq. 50),
+//   * the deformation-state form (Section 3.3): terminal sampling of I0 at the
+//     inverse map, its force fields, and the padded-grid products of the
+//     band-limited deformation sweep.
 // One thread per grid point or band slot; the transport kernels are bound by
 // HBM traffic (coalesced streams plus an L1/L2-served 8-corner gather).
 #include "internal.h"
@@ -429,6 +432,117 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const double* partial, in
   if (threadIdx.x == 0) *out = acc;
 }
 
+
+// ---- deformation-state form (Section 3.3) ------------------------------------
+// central-difference gradient of an image, [3][vol]
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_central_grad(const T* __restrict__ m, T* __restrict__ g3, Dims g) {
+  const long long vol = g.vol();
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= vol) return;
+  int ix[3];
+  unflat(idx, g.n2, g.n3, ix);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) g3[j * vol + idx] = cdiff(m, ix, j, g);
+}
+
+// m(1)(x) = I0(x + u(x)) and gs(x) = (grad I0)(x + u(x)), both by periodic
+// trilinear interpolation; u is the grid displacement in unit-box units
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_def_sample(const T* __restrict__ I0, const T* __restrict__ gI0, const T* __restrict__ u,
+             T* __restrict__ m1, T* __restrict__ gs, Dims g) {
+  const long long vol = g.vol();
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= vol) return;
+  int ix[3];
+  unflat(idx, g.n2, g.n3, ix);
+  const int n[3] = {g.n1, g.n2, g.n3};
+  T w[3];
+  int c0[3], c1[3], o[8];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) cell(ix[j], -u[j * vol + idx] * T(n[j]), n[j], c0[j], c1[j], w[j]);
+  corners(c0, c1, g.n2, g.n3, o);
+  m1[idx] = trilin(I0, o, w);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) gs[j * vol + idx] = trilin(gI0 + j * vol, o, w);
+}
+
+// terminal force of the deformation form on the image grid, f = [3][vol]:
+//   du == nullptr:  f = c (m1 - I1) gs             (lambda(1) grad I0 o phi^-1, c = -2/sigma^2)
+//   otherwise:      dm = gs . du,  f = c dm gs     (its Gauss-Newton increment); dm -> dm_out
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_def_force(const T* __restrict__ gs, const T* __restrict__ m1, const T* __restrict__ I1,
+            const T* __restrict__ du, T* __restrict__ dm_out, T c, T* __restrict__ f, long long vol) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= vol) return;
+  const T g0 = gs[idx], g1 = gs[vol + idx], g2 = gs[2 * vol + idx];
+  T a;
+  if (du == nullptr) {
+    a = c * (m1[idx] - I1[idx]);
+  } else {
+    const T dm = fma(g0, du[idx], fma(g1, du[vol + idx], g2 * du[2 * vol + idx]));
+    if (dm_out) dm_out[idx] = dm;
+    a = c * dm;
+  }
+  f[idx] = a * g0;
+  f[vol + idx] = a * g1;
+  f[2 * vol + idx] = a * g2;
+}
+
+// pointwise products of the deformation form on the padded grid; fields are
+// [F][vol] with Jacobian blocks D[3 i + j] = d_j a_i:
+//   mode 0:  out_i = -(v_i + sum_j D_ij v_j)                      F = {D u, v}
+//   mode 1:  out_i = -(dv_i + sum_j dD_ij v_j + D_ij dv_j)         F = {D du, v, D u, dv}
+//   mode 2:  out_i = r_i + sum_j D_ji r_j                           F = {D u, r}
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_def_products(int mode, const T* __restrict__ fl, T* __restrict__ out, long long vol) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= vol) return;
+  T D[9], v[3];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) D[q] = fl[q * vol + idx];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) v[j] = fl[(9 + j) * vol + idx];
+  if (mode == 2) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      T acc = v[i];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) acc = fma(D[3 * j + i], v[j], acc);
+      out[i * vol + idx] = acc;
+    }
+    return;
+  }
+  T acc[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    acc[i] = T(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) acc[i] = fma(D[3 * i + j], v[j], acc[i]);
+  }
+  if (mode == 0) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[i * vol + idx] = -(v[i] + acc[i]);
+    return;
+  }
+  T E[9], dv[3];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) E[q] = fl[(12 + q) * vol + idx];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) dv[j] = fl[(21 + j) * vol + idx];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T a = acc[i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) a = fma(E[3 * i + j], dv[j], a);
+    out[i * vol + idx] = -(dv[i] + a);
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -515,7 +629,33 @@ void inner_V(const cplx<T>* a, const cplx<T>* b, const T* Lhat, int ncomp, long 
   k_finalize<<<1, kThreads, 0, st>>>(partial, kReduceBlocks, out);
 }
 
+template <typename T>
+void central_grad(const T* m, T* g3, Dims g, cudaStream_t st) {
+  k_central_grad<T><<<blocks_for(g.vol()), kThreads, 0, st>>>(m, g3, g);
+}
+
+template <typename T>
+void def_sample(const T* I0, const T* gI0, const T* u, T* m1, T* gs, Dims g, cudaStream_t st) {
+  k_def_sample<T><<<blocks_for(g.vol()), kThreads, 0, st>>>(I0, gI0, u, m1, gs, g);
+}
+
+template <typename T>
+void def_force(const T* gs, const T* m1, const T* I1, const T* du, T* dm_out, double c, T* f, long long vol,
+               cudaStream_t st) {
+  k_def_force<T><<<blocks_for(vol), kThreads, 0, st>>>(gs, m1, I1, du, dm_out, (T)c, f, vol);
+}
+
+template <typename T>
+void def_products(int mode, const T* fields, T* out, long long vol, cudaStream_t st) {
+  k_def_products<T><<<blocks_for(vol), kThreads, 0, st>>>(mode, fields, out, vol);
+}
+
 #define LDDMM_INST(T)                                                                              \
+  template void central_grad<T>(const T*, T*, Dims, cudaStream_t);                                 \
+  template void def_sample<T>(const T*, const T*, const T*, T*, T*, Dims, cudaStream_t);           \
+  template void def_force<T>(const T*, const T*, const T*, const T*, T*, double, T*, long long,    \
+                             cudaStream_t);                                                        \
+  template void def_products<T>(int, const T*, T*, long long, cudaStream_t);                       \
   template void transport_step<T>(const T*, const T*, const T*, T*, T*, Dims, double,            \
                                   cudaStream_t);                                                 \
   template void grad_dot<T>(const T*, const T*, T*, Dims, cudaStream_t);                         \

@@ -214,6 +214,25 @@ void inc_step(const T* dm, const T* s, const T* mnext, const T* dvnext, const T*
 template <typename T>
 void terminal_field(const T* m, const T* y, int diff, double coef, T* out, Dims g,
                     cudaStream_t st);
+// ---- deformation-state form (Section 3.3) ----
+// central-difference gradient of an image -> [3][vol]
+template <typename T>
+void central_grad(const T* m, T* g3, Dims g, cudaStream_t st);
+// m1(x) = I0(x + u(x)), gs(x) = (grad I0)(x + u(x)) (trilinear, periodic); u [3][vol]
+// in unit-box units
+template <typename T>
+void def_sample(const T* I0, const T* gI0, const T* u, T* m1, T* gs, Dims g, cudaStream_t st);
+// f = c (m1 - I1) gs (du == nullptr), else dm = gs . du (-> dm_out if given) and
+// f = c dm gs; f [3][vol]
+template <typename T>
+void def_force(const T* gs, const T* m1, const T* I1, const T* du, T* dm_out, double c, T* f, long long vol,
+               cudaStream_t st);
+// padded-grid products (Jacobian blocks D[3 i + j] = d_j a_i, fields [F][vol]):
+//   0: out_i = -(v_i + D_ij v_j)                 fields {D u, v}
+//   1: out_i = -(dv_i + dD_ij v_j + D_ij dv_j)    fields {D du, v, D u, dv}
+//   2: out_i = r_i + D_ji r_j                     fields {D u, r}
+template <typename T>
+void def_products(int mode, const T* fields, T* out, long long vol, cudaStream_t st);
 // one reversed step of the exact discrete adjoint of the state transport:
 // lam_out (zeroed by the caller) and gcur gain atomic scatters, gnext gains the
 // per-voxel terms (see grid.cu); off is the step's stored displacement.

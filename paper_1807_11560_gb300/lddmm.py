@@ -32,7 +32,8 @@ class Opts(ctypes.Structure):
                 ("pcg_tol", ctypes.c_double), ("armijo_c", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("persistent", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("recompute", ctypes.c_int), ("autotune", ctypes.c_int), ("newton", ctypes.c_int)]
+                ("recompute", ctypes.c_int), ("autotune", ctypes.c_int), ("newton", ctypes.c_int),
+                ("state_eq", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -170,11 +171,13 @@ class Context:
 
     grid, K: per-axis image and band sizes (2 or 3 axes); alpha, s: L =
     (Id - alpha Lap)^s; sigma: data weight 1/sigma^2; Nt: time steps.
+    state: "image" (the image state equation, Section 3.2) or "deformation"
+    (the band-limited deformation state equation, Section 3.3).
     """
 
     def __init__(self, grid, K, alpha, s, sigma, Nt, precision="fp32", stream=None,
                  use_graphs=True, pcg_tol=1e-12, armijo_c=1e-4, max_halvings=10, persistent="auto",
-                 tensor_cores="auto", recompute=False, autotune=True, newton=False):
+                 tensor_cores="auto", recompute=False, autotune=True, newton=False, state="image"):
         L = lib()
         self.grid, self.K = tuple(int(g) for g in grid), tuple(int(k) for k in K)
         self.ndim = len(self.grid)
@@ -191,6 +194,7 @@ class Context:
         o.recompute = 1 if recompute else 0
         o.autotune = 1 if autotune else 0
         o.newton = 1 if newton else 0
+        o.state_eq = {"image": 0, "deformation": 1}[state]
         o.pcg_tol, o.armijo_c, o.max_halvings = pcg_tol, armijo_c, max_halvings
         arr = ctypes.c_int * self.ndim
         h = ctypes.c_void_p()
