@@ -9,7 +9,11 @@
 //     (v, Dv, L v, D(L v)) of every Heun stage point, the grid velocities
 //     iota(v_n), the state history m_n and the characteristic displacements;
 //   * the tangent history dv_n and its grid velocities, two ping-pong pairs
-//     for dm and s = grad m . dv, the transform scratch and BL temporaries.
+//     for dm and s = grad m . dv, the transform scratch and BL temporaries;
+//   * with the deformation state equation (Section 3.3, opts.state_eq = 1):
+//     per trajectory the band-limited inverse-map displacement u_n and its
+//     predictors, the padded-grid fields {D u, v} of lin's stage points, and
+//     grad I0 on the image grid.
 // The time loops run on the host and enqueue kernels on one stream; the
 // Hessian-vector product can be captured once per linearisation point into a
 // CUDA graph and replayed.
@@ -82,7 +86,7 @@ struct Impl {
   C *T2 = nullptr, *P2 = nullptr;
   C *k1 = nullptr, *aU = nullptr, *aW = nullptr, *Ut = nullptr, *Wt = nullptr, *U = nullptr,
     *W = nullptr, *dstar = nullptr, *vin = nullptr, *vout = nullptr, *gbuf = nullptr;
-  C *px = nullptr, *pr = nullptr, *pd = nullptr, *pq = nullptr, *vsol = nullptr, *vtry = nullptr;
+  C *px = nullptr, *pr = nullptr, *vsol = nullptr, *vtry = nullptr;
   C* dvh = nullptr;          // [Nt+1][3][Kvol]
   C* srcs = nullptr;         // [Nt+1][3][Kvol] band sources of the exact discrete adjoint
   C* dvsh = nullptr;         // [Nt][3][Kvol] tangent predictor stages dv*_n
@@ -113,7 +117,8 @@ struct Impl {
   bool have_zhist = false;   // Uh/Wh/Uth/Wth hold the last gradient's backward sweep
   // deformation-state form (Section 3.3)
   T* gI0 = nullptr;           // [3][Nvol] central-difference gradient of I0
-  T* defM = nullptr;          // [24][Mvol] padded-grid fields of the deformation products
+  T* defM = nullptr;          // [12][Mvol] padded-grid fields of the deformation products
+  T* defcache = nullptr;      // [2 Nt][12][Mvol] {D u, v} at the stage points of lin's sweep
   T* prodM = nullptr;         // [3][Mvol] their products
   C *dk1 = nullptr, *rhob = nullptr, *dua = nullptr, *dub = nullptr, *dup = nullptr;   // [3][Kvol]
   cudaStream_t cap = nullptr;
@@ -390,7 +395,7 @@ struct Impl {
     const long long t2 = std::max(33LL * H1 * N.n2 * N.n3, 24LL * H1 * M.n2 * M.n3);
     alloc(T2, (size_t)t2);
     alloc(P2, (size_t)9 * H1 * M.n2 * M.n3);
-    for (C** b : {&k1, &aU, &aW, &Ut, &Wt, &U, &W, &dstar, &vin, &vout, &gbuf, &px, &pr, &pd, &pq,
+    for (C** b : {&k1, &aU, &aW, &Ut, &Wt, &U, &W, &dstar, &vin, &vout, &gbuf, &px, &pr,
                   &vsol, &vtry})
       alloc(*b, (size_t)3 * Kvol);
     alloc(dvh, (size_t)(Nt + 1) * 3 * Kvol);
@@ -412,7 +417,8 @@ struct Impl {
     alloc(fterm, (size_t)3 * Nvol);
     if (deform()) {
       alloc(gI0, (size_t)3 * Nvol);
-      alloc(defM, (size_t)24 * Mvol);
+      alloc(defM, (size_t)12 * Mvol);
+      alloc(defcache, (size_t)2 * Nt * 12 * Mvol);
       alloc(prodM, (size_t)3 * Mvol);
       for (C** b : {&dk1, &rhob, &dua, &dub, &dup}) alloc(*b, (size_t)3 * Kvol);
     }
@@ -818,22 +824,24 @@ struct Impl {
     const double H1 = K.h1, K2 = K.k2, K3 = K.k3;
     return nf * (8.0 * H1 * (K2 * K3 * g.n3 + K2 * (double)g.n2 * g.n3) + 4.0 * H1 * (double)g.vol());
   }
-  // one padded-grid product of the deformation form (def_products mode) with
-  // its iota fields {D a, b} (and {D a2, b2} for mode 1) and pi epilogue e
-  void def_eval(int mode, const C* a, const C* b, const C* a2, const C* b2, const PiEpi<T>& e) {
+  // one padded-grid product of the deformation form (def_products mode): iota
+  // of the fields {D a, b} into fl (defM when null), the product (mode 1 with
+  // the cached stage-point block {D u, v}) and pi with epilogue e
+  void def_eval(int mode, const C* a, const C* b, const PiEpi<T>& e, T* fl = nullptr,
+                const T* cached = nullptr) {
+    if (!fl) fl = defM;
     IotaDesc<T> d{};
-    d.nf = mode == 1 ? 24 : 12;
+    d.nf = 12;
     jac_val(d, 0, a, b);
-    if (mode == 1) jac_val(d, 12, a2, b2);
-    for (int f = 0; f < d.nf; ++f) d.dst[f] = defM + (long long)f * Mvol;
+    for (int f = 0; f < d.nf; ++f) d.dst[f] = fl + (long long)f * Mvol;
     PiSrc<T> ps{};
     ps.nf = 3;
     for (int c = 0; c < 3; ++c) ps.src[c] = prodM + (long long)c * Mvol;
     pb(PR_DEFORM);
     iota_batch<T>(pad, d, Lhat, T2, st, nullptr);
-    def_products<T>(mode, defM, prodM, Mvol, st);
+    def_products<T>(mode, fl, cached, prodM, Mvol, st);
     pi_batch<T>(pad, ps, e, Lhat, T2, st);
-    pe(PR_DEFORM, grid_flops(M, d.nf + 3) + (mode == 1 ? 42.0 : 21.0) * (double)Mvol);
+    pe(PR_DEFORM, grid_flops(M, d.nf + 3) + (mode == 1 ? 36.0 : 18.0) * (double)Mvol);
     launches += kIotaLaunches + 1 + kPiLaunches;
     check_launch("deformation product");
   }
@@ -845,9 +853,14 @@ struct Impl {
     return e;
   }
 
+  // padded-grid block {D u, v} of stage point k (2 n, 2 n + 1) of lin's sweep
+  T* def_slot(int k) { return defcache + (long long)k * 12 * Mvol; }
+
   // Heun sweep of d/dt u~ = -v~ - D~u~ * v~ jointly with the shoot (stage 2 at
-  // the EPDiff predictor v*_n), u~(0) = 0
+  // the EPDiff predictor v*_n), u~(0) = 0.  For lin the padded-grid fields of
+  // each stage point stay in defcache for the tangent sweeps.
   void deform_sweep(State<T>& S) {
+    const bool keep = &S == &lin;
     cuda(cudaMemsetAsync(S.uh, 0, (size_t)3 * Kvol * sizeof(C), st), "memset u0");
     for (int n = 0; n < Nt; ++n) {
       C* un = vec(S.uh, n);
@@ -855,10 +868,10 @@ struct Impl {
       PiEpi<T> e1 = def_epi(false);
       add_out(e1, dk1, 0, 1.0, {});
       add_out(e1, us, 0, dt, {{un, 1.0}});
-      def_eval(0, un, vec(S.vh, n), nullptr, nullptr, e1);
+      def_eval(0, un, vec(S.vh, n), e1, keep ? def_slot(2 * n) : nullptr);
       PiEpi<T> e2 = def_epi(false);
       add_out(e2, vec(S.uh, n + 1), 0, 0.5 * dt, {{un, 1.0}, {dk1, 0.5 * dt}});
-      def_eval(0, us, vec(S.vsh, n), nullptr, nullptr, e2);
+      def_eval(0, us, vec(S.vsh, n), e2, keep ? def_slot(2 * n + 1) : nullptr);
     }
   }
 
@@ -872,9 +885,10 @@ struct Impl {
     check_launch("deformation terminal sampling");
   }
 
-  // exact tangent of the deformation sweep along the shoot tangent (dvh, dvsh);
-  // returns the buffer holding delta u~(1)
-  C* deform_tangent(State<T>& S) {
+  // exact tangent of lin's deformation sweep along the shoot tangent (dvh,
+  // dvsh), reading {D u, v} of each stage point from defcache; returns the
+  // buffer holding delta u~(1)
+  C* deform_tangent() {
     C* cur = dua;
     C* nxt = dub;
     cuda(cudaMemsetAsync(cur, 0, (size_t)3 * Kvol * sizeof(C), st), "memset du0");
@@ -882,10 +896,10 @@ struct Impl {
       PiEpi<T> e1 = def_epi(false);
       add_out(e1, dk1, 0, 1.0, {});
       add_out(e1, dup, 0, dt, {{cur, 1.0}});
-      def_eval(1, cur, vec(S.vh, n), vec(S.uh, n), vec(dvh, n), e1);
+      def_eval(1, cur, vec(dvh, n), e1, nullptr, def_slot(2 * n));
       PiEpi<T> e2 = def_epi(false);
       add_out(e2, nxt, 0, 0.5 * dt, {{cur, 1.0}, {dk1, 0.5 * dt}});
-      def_eval(1, dup, vec(S.vsh, n), vec(S.ush, n), vec(dvsh, n), e2);
+      def_eval(1, dup, vec(dvsh, n), e2, nullptr, def_slot(2 * n + 1));
       std::swap(cur, nxt);
     }
     return cur;
@@ -895,7 +909,7 @@ struct Impl {
   void terminal_deform(const C* r, const C* u, C* out) {
     PiEpi<T> e = def_epi(true);
     add_out(e, out, 0, 1.0, {});
-    def_eval(2, u, r, nullptr, nullptr, e);
+    def_eval(2, u, r, e);
   }
 
   // energy pieces into dres[0] (<v0,v0>_V) and dres[1] (sum (m1 - I1)^2)
@@ -1140,7 +1154,7 @@ struct Impl {
     State<T>& S = lin;
     if (deform()) {                           // Section 3.3 under Gauss-Newton
       tangent(S);
-      const C* du1 = deform_tangent(S);
+      const C* du1 = deform_tangent();
       to_grid(du1, 1, dvgrid);
       def_force<T>(S.vgrid, m1(S), I1, dvgrid, dm[Nt & 1], -2.0 / (sigma * sigma), fterm, Nvol, st);
       ++launches;
@@ -1422,30 +1436,23 @@ struct Impl {
       }
       r.gnorm_final = gn;
       if (r.E_hist) r.E_hist[it] = E;
-      // CG in the V inner product on H p = -g (Eq. 45)
+      // CG in the V inner product on H p = -g (Eq. 45).  The direction is kept
+      // in the product's input slot dvh[0] (no sweep writes it) and q is read
+      // from the product's output, so no vector is copied per iteration.
+      const long long n3 = 3 * Kvol;
       cuda(cudaMemsetAsync(px, 0, bytes, st), "memset");
-      axpby<T>(pr, -1.0, gbuf, 0.0, nullptr, 3 * Kvol, st);
-      cuda(cudaMemcpyAsync(pd, pr, bytes, cudaMemcpyDeviceToDevice, st), "copy");
+      axpby<T>(pr, -1.0, gbuf, 0.0, nullptr, n3, st);
+      cuda(cudaMemcpyAsync(dvh, pr, bytes, cudaMemcpyDeviceToDevice, st), "copy");
       ++launches;
       // the scalars stay on the device; the host looks at the stop flag every
       // fourth iteration (iterations after a stop only repeat the product)
       inner_V<T>(pr, pr, Lhat, 3, Kvol, partial, dpcg + PCG_R, st);
       pcg_init(dpcg, st);
       launches += 3;
-      const long long n3 = 3 * Kvol;
       for (int k = 1; k <= n_pcg; ++k) {
-        cuda(cudaMemcpyAsync(dvh, pd, bytes, cudaMemcpyDeviceToDevice, st), "copy");
         hessvec_dev(opts.newton != 0);
-        cuda(cudaMemcpyAsync(pq, vout, bytes, cudaMemcpyDeviceToDevice, st), "copy");
-        inner_V<T>(pd, pq, Lhat, 3, Kvol, partial, dpcg + PCG_DQ, st);
-        pcg_alpha(dpcg, st);
-        copy_if<T>(px, pd, dpcg, n3, st);
-        axpy_dev<T>(px, px, pd, dpcg, PCG_A, 1.0, n3, st);
-        axpy_dev<T>(pr, pr, pq, dpcg, PCG_A, -1.0, n3, st);
-        inner_V<T>(pr, pr, Lhat, 3, Kvol, partial, dpcg + PCG_RN, st);
-        pcg_beta(dpcg, opts.pcg_tol, st);
-        axpy_dev<T>(pd, pr, pd, dpcg, PCG_BETA, 1.0, n3, st);
-        launches += 10;
+        pcg_step<T>(px, pr, dvh, vout, Lhat, Kvol, 3, partial, dpcg, opts.pcg_tol, st);
+        launches += 5;
         if (k % 4 == 0 && k < n_pcg) {
           cuda(cudaMemcpyAsync(hres, dpcg + PCG_DONE, sizeof(double), cudaMemcpyDeviceToHost, st), "read");
           sync("pcg");

@@ -305,40 +305,6 @@ __global__ void k_pcg_init(double* s) {
   s[PCG_COPY] = 0.0;
 }
 
-// after <d, Hd>: alpha = rho / <d, Hd>, or stop at non-positive curvature (the
-// first iteration then returns x = d, the steepest-descent direction)
-__global__ void k_pcg_alpha(double* s) {
-  const double k = s[PCG_K] + 1.0;
-  s[PCG_K] = k;
-  s[PCG_COPY] = 0.0;
-  if (s[PCG_DONE] != 0.0) {
-    s[PCG_A] = 0.0;
-    return;
-  }
-  const double dq = s[PCG_DQ];
-  if (!(dq > 0.0)) {
-    s[PCG_DONE] = 1.0;
-    s[PCG_ITS] = k - 1.0;
-    if (k == 1.0) s[PCG_COPY] = 1.0;
-    s[PCG_A] = 0.0;
-    return;
-  }
-  s[PCG_A] = s[PCG_R] / dq;
-}
-
-// after rho_new: stop on the relative residual, else beta = rho_new / rho
-__global__ void k_pcg_beta(double* s, double tol) {
-  if (s[PCG_DONE] != 0.0) return;
-  s[PCG_ITS] = s[PCG_K];
-  const double rn = s[PCG_RN];
-  if (sqrt(rn) <= tol * s[PCG_B]) {
-    s[PCG_DONE] = 1.0;
-    return;
-  }
-  s[PCG_BETA] = rn / s[PCG_R];
-  s[PCG_R] = rn;
-}
-
 // out = x + sign s[ci] y unless stopped
 template <typename T>
 __global__ void k_axpy_dev(cplx<T>* out, const cplx<T>* x, const cplx<T>* y, const double* s, int ci, double sign,
@@ -351,13 +317,6 @@ __global__ void k_axpy_dev(cplx<T>* out, const cplx<T>* x, const cplx<T>* y, con
   v.x = fma(b, y[i].x, v.x);
   v.y = fma(b, y[i].y, v.y);
   out[i] = v;
-}
-
-template <typename T>
-__global__ void k_copy_if(cplx<T>* out, const cplx<T>* in, const double* s, long long n) {
-  if (s[PCG_COPY] == 0.0) return;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = in[i];
 }
 
 template <typename T>
@@ -493,20 +452,22 @@ k_def_force(const T* __restrict__ gs, const T* __restrict__ m1, const T* __restr
 }
 
 // pointwise products of the deformation form on the padded grid; fields are
-// [F][vol] with Jacobian blocks D[3 i + j] = d_j a_i:
-//   mode 0:  out_i = -(v_i + sum_j D_ij v_j)                      F = {D u, v}
-//   mode 1:  out_i = -(dv_i + sum_j dD_ij v_j + D_ij dv_j)         F = {D du, v, D u, dv}
-//   mode 2:  out_i = r_i + sum_j D_ji r_j                           F = {D u, r}
+// [12][vol] blocks {Jacobian D[3 i + j] = d_j a_i, values}:
+//   mode 0:  out_i = -(v_i + sum_j D_ij v_j)                      fl = {D u, v}
+//   mode 1:  out_i = -(dv_i + sum_j dD_ij v_j + D_ij dv_j)         fl = {D du, dv}, fc = {D u, v}
+//   mode 2:  out_i = r_i + sum_j D_ji r_j                           fl = {D u, r}
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_def_products(int mode, const T* __restrict__ fl, T* __restrict__ out, long long vol) {
+k_def_products(int mode, const T* __restrict__ fl, const T* __restrict__ fc, T* __restrict__ out,
+               long long vol) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= vol) return;
+  const T* src = mode == 1 ? fc : fl;       // the block holding D u and v (or r)
   T D[9], v[3];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) D[q] = fl[q * vol + idx];
+  for (int q = 0; q < 9; ++q) D[q] = src[q * vol + idx];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) v[j] = fl[(9 + j) * vol + idx];
+  for (int j = 0; j < 3; ++j) v[j] = src[(9 + j) * vol + idx];
   if (mode == 2) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -517,30 +478,104 @@ k_def_products(int mode, const T* __restrict__ fl, T* __restrict__ out, long lon
     }
     return;
   }
-  T acc[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    acc[i] = T(0);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) acc[i] = fma(D[3 * i + j], v[j], acc[i]);
-  }
   if (mode == 0) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) out[i * vol + idx] = -(v[i] + acc[i]);
+    for (int i = 0; i < 3; ++i) {
+      T a = T(0);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) a = fma(D[3 * i + j], v[j], a);
+      out[i * vol + idx] = -(v[i] + a);
+    }
     return;
   }
-  T E[9], dv[3];
+  T dD[9], dv[3];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) E[q] = fl[(12 + q) * vol + idx];
+  for (int q = 0; q < 9; ++q) dD[q] = fl[q * vol + idx];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) dv[j] = fl[(21 + j) * vol + idx];
+  for (int j = 0; j < 3; ++j) dv[j] = fl[(9 + j) * vol + idx];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    T a = acc[i];
+    T a = T(0);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) a = fma(E[3 * i + j], dv[j], a);
+    for (int j = 0; j < 3; ++j) a = fma(dD[3 * i + j], v[j], fma(D[3 * i + j], dv[j], a));
     out[i * vol + idx] = -(dv[i] + a);
   }
+}
+
+
+// ---- PCG steps with the scalar logic folded into the reductions ---------------
+// <d, q>_V from the block partials, then alpha, or the stop at non-positive
+// curvature (a stop on the first iteration returns x = d, the steepest-descent
+// direction)
+__global__ void __launch_bounds__(kThreads) k_finalize_alpha(const double* partial, int n, double* s) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += kThreads) acc += partial[i];
+  acc = block_sum(acc);
+  if (threadIdx.x != 0) return;
+  const double k = s[PCG_K] + 1.0;
+  s[PCG_K] = k;
+  s[PCG_COPY] = 0.0;
+  s[PCG_DQ] = acc;
+  if (s[PCG_DONE] != 0.0) {
+    s[PCG_A] = 0.0;
+    return;
+  }
+  if (!(acc > 0.0)) {
+    s[PCG_DONE] = 1.0;
+    s[PCG_ITS] = k - 1.0;
+    if (k == 1.0) s[PCG_COPY] = 1.0;
+    s[PCG_A] = 0.0;
+    return;
+  }
+  s[PCG_A] = s[PCG_R] / acc;
+}
+
+// x = d on a first-iteration curvature stop; else (unless stopped) x += alpha d,
+// r -= alpha q; block partials of <r, r>_V
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_pcg_xr(cplx<T>* __restrict__ x, cplx<T>* __restrict__ r, const cplx<T>* __restrict__ d,
+         const cplx<T>* __restrict__ q, const T* __restrict__ L, long long kvol, long long n,
+         const double* s, double* partial) {
+  const bool copy = s[PCG_COPY] != 0.0;
+  const bool done = s[PCG_DONE] != 0.0;
+  const T a = (T)s[PCG_A];
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (copy) x[i] = d[i];
+    if (done) continue;
+    cplx<T> xv = x[i], rv = r[i];
+    const cplx<T> dv = d[i], qv = q[i];
+    xv.x = fma(a, dv.x, xv.x);
+    xv.y = fma(a, dv.y, xv.y);
+    rv.x = fma(-a, qv.x, rv.x);
+    rv.y = fma(-a, qv.y, rv.y);
+    x[i] = xv;
+    r[i] = rv;
+    const double l = (double)L[i % kvol];
+    acc = fma(l, (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y, acc);
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// <r, r>_V from the block partials, then the stop on the relative residual
+// ||r||_V <= tol ||b||_V, or beta = rho_new / rho
+__global__ void __launch_bounds__(kThreads) k_finalize_beta(const double* partial, int n, double* s, double tol) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += kThreads) acc += partial[i];
+  acc = block_sum(acc);
+  if (threadIdx.x != 0) return;
+  s[PCG_RN] = acc;
+  if (s[PCG_DONE] != 0.0) return;
+  s[PCG_ITS] = s[PCG_K];
+  if (sqrt(acc) <= tol * s[PCG_B]) {
+    s[PCG_DONE] = 1.0;
+    return;
+  }
+  s[PCG_BETA] = acc / s[PCG_R];
+  s[PCG_R] = acc;
 }
 
 }  // namespace
@@ -597,19 +632,6 @@ void axpby(cplx<T>* out, double a, const cplx<T>* x, double bcoef, const cplx<T>
 }
 
 void pcg_init(double* s, cudaStream_t st) { k_pcg_init<<<1, 1, 0, st>>>(s); }
-void pcg_alpha(double* s, cudaStream_t st) { k_pcg_alpha<<<1, 1, 0, st>>>(s); }
-void pcg_beta(double* s, double tol, cudaStream_t st) { k_pcg_beta<<<1, 1, 0, st>>>(s, tol); }
-
-template <typename T>
-void axpy_dev(cplx<T>* out, const cplx<T>* x, const cplx<T>* y, const double* s, int ci, double sign, long long n,
-              cudaStream_t st) {
-  k_axpy_dev<T><<<blocks_for(n), kThreads, 0, st>>>(out, x, y, s, ci, sign, n);
-}
-
-template <typename T>
-void copy_if(cplx<T>* out, const cplx<T>* in, const double* s, long long n, cudaStream_t st) {
-  k_copy_if<T><<<blocks_for(n), kThreads, 0, st>>>(out, in, s, n);
-}
 
 template <typename T>
 void scale_L(cplx<T>* out, const cplx<T>* x, const T* Lhat, int ncomp, long long kvol, cudaStream_t st) {
@@ -630,6 +652,17 @@ void inner_V(const cplx<T>* a, const cplx<T>* b, const T* Lhat, int ncomp, long 
 }
 
 template <typename T>
+void pcg_step(cplx<T>* x, cplx<T>* r, cplx<T>* d, const cplx<T>* q, const T* Lhat, long long kvol, int ncomp,
+              double* partial, double* s, double tol, cudaStream_t st) {
+  const long long n = ncomp * kvol;
+  k_inner_V<T><<<kReduceBlocks, kThreads, 0, st>>>(d, q, Lhat, kvol, n, partial);
+  k_finalize_alpha<<<1, kThreads, 0, st>>>(partial, kReduceBlocks, s);
+  k_pcg_xr<T><<<kReduceBlocks, kThreads, 0, st>>>(x, r, d, q, Lhat, kvol, n, s, partial);
+  k_finalize_beta<<<1, kThreads, 0, st>>>(partial, kReduceBlocks, s, tol);
+  k_axpy_dev<T><<<blocks_for(n), kThreads, 0, st>>>(d, r, d, s, PCG_BETA, 1.0, n);
+}
+
+template <typename T>
 void central_grad(const T* m, T* g3, Dims g, cudaStream_t st) {
   k_central_grad<T><<<blocks_for(g.vol()), kThreads, 0, st>>>(m, g3, g);
 }
@@ -646,16 +679,18 @@ void def_force(const T* gs, const T* m1, const T* I1, const T* du, T* dm_out, do
 }
 
 template <typename T>
-void def_products(int mode, const T* fields, T* out, long long vol, cudaStream_t st) {
-  k_def_products<T><<<blocks_for(vol), kThreads, 0, st>>>(mode, fields, out, vol);
+void def_products(int mode, const T* fields, const T* cached, T* out, long long vol, cudaStream_t st) {
+  k_def_products<T><<<blocks_for(vol), kThreads, 0, st>>>(mode, fields, cached, out, vol);
 }
 
 #define LDDMM_INST(T)                                                                              \
+  template void pcg_step<T>(cplx<T>*, cplx<T>*, cplx<T>*, const cplx<T>*, const T*, long long, int,  \
+                            double*, double*, double, cudaStream_t);                                \
   template void central_grad<T>(const T*, T*, Dims, cudaStream_t);                                 \
   template void def_sample<T>(const T*, const T*, const T*, T*, T*, Dims, cudaStream_t);           \
   template void def_force<T>(const T*, const T*, const T*, const T*, T*, double, T*, long long,    \
                              cudaStream_t);                                                        \
-  template void def_products<T>(int, const T*, T*, long long, cudaStream_t);                       \
+  template void def_products<T>(int, const T*, const T*, T*, long long, cudaStream_t);            \
   template void transport_step<T>(const T*, const T*, const T*, T*, T*, Dims, double,            \
                                   cudaStream_t);                                                 \
   template void grad_dot<T>(const T*, const T*, T*, Dims, cudaStream_t);                         \
@@ -670,9 +705,6 @@ void def_products(int mode, const T* fields, T* out, long long vol, cudaStream_t
   template void axpby<T>(cplx<T>*, double, const cplx<T>*, double, const cplx<T>*, long long,    \
                          cudaStream_t);                                                          \
   template void scale_L<T>(cplx<T>*, const cplx<T>*, const T*, int, long long, cudaStream_t);    \
-  template void axpy_dev<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const double*, int, double,  \
-                            long long, cudaStream_t);                                              \
-  template void copy_if<T>(cplx<T>*, const cplx<T>*, const double*, long long, cudaStream_t);     \
   template void sum_sq_diff<T>(const T*, const T*, long long, double*, double*, cudaStream_t);   \
   template void inner_V<T>(const cplx<T>*, const cplx<T>*, const T*, int, long long, double*,    \
                            double*, cudaStream_t);

@@ -227,12 +227,13 @@ void def_sample(const T* I0, const T* gI0, const T* u, T* m1, T* gs, Dims g, cud
 template <typename T>
 void def_force(const T* gs, const T* m1, const T* I1, const T* du, T* dm_out, double c, T* f, long long vol,
                cudaStream_t st);
-// padded-grid products (Jacobian blocks D[3 i + j] = d_j a_i, fields [F][vol]):
+// padded-grid products (blocks of 12 fields [12][vol]: Jacobian D[3 i + j] = d_j a_i,
+// then 3 values):
 //   0: out_i = -(v_i + D_ij v_j)                 fields {D u, v}
-//   1: out_i = -(dv_i + dD_ij v_j + D_ij dv_j)    fields {D du, v, D u, dv}
+//   1: out_i = -(dv_i + dD_ij v_j + D_ij dv_j)    fields {D du, dv}, cached {D u, v}
 //   2: out_i = r_i + D_ji r_j                     fields {D u, r}
 template <typename T>
-void def_products(int mode, const T* fields, T* out, long long vol, cudaStream_t st);
+void def_products(int mode, const T* fields, const T* cached, T* out, long long vol, cudaStream_t st);
 // one reversed step of the exact discrete adjoint of the state transport:
 // lam_out (zeroed by the caller) and gcur gain atomic scatters, gnext gains the
 // per-voxel terms (see grid.cu); off is the step's stored displacement.
@@ -269,12 +270,11 @@ constexpr int kReduceBlocks = 304;   // 2 x 152 SMs
 enum PcgSlot { PCG_R = 0, PCG_B, PCG_DQ, PCG_A, PCG_RN, PCG_BETA, PCG_DONE, PCG_ITS, PCG_K, PCG_COPY,
                PCG_SLOTS = 16 };
 void pcg_init(double* s, cudaStream_t st);                 // ||b|| = sqrt(rho), counters reset
-void pcg_alpha(double* s, cudaStream_t st);                // alpha or the curvature stop
-void pcg_beta(double* s, double tol, cudaStream_t st);     // residual stop or beta
-template <typename T>                                      // out = x + sign s[ci] y unless stopped
-void axpy_dev(cplx<T>* out, const cplx<T>* x, const cplx<T>* y, const double* s, int ci, double sign, long long n,
-              cudaStream_t st);
-template <typename T>                                      // out = in if s[PCG_COPY]
-void copy_if(cplx<T>* out, const cplx<T>* in, const double* s, long long n, cudaStream_t st);
+// one whole PCG step after q = H d in five launches: <d, q>_V partials; alpha
+// (or the curvature stop) folded into their sum; x, r updates with the
+// <r, r>_V partials; beta (or the residual stop) folded into their sum; d
+template <typename T>
+void pcg_step(cplx<T>* x, cplx<T>* r, cplx<T>* d, const cplx<T>* q, const T* Lhat, long long kvol, int ncomp,
+              double* partial, double* s, double tol, cudaStream_t st);
 
 }  // namespace lddmm
