@@ -168,3 +168,94 @@ def test_incremental_transport_converges_to_derivative_of_transport():
         gaps.append(np.sqrt(np.mean((dm - fd) ** 2) / np.mean(fd ** 2)))
     assert gaps[0] > gaps[1] > gaps[2]
     assert gaps[2] < 0.06, gaps
+
+
+# ---- the characteristic of the state transport at time- and space-varying
+# velocity.  Fields built from the periodic triangle wave tri (slope 1 on
+# [-1/4, 1/4], slope -1 on [1/4, 3/4], kinks on grid nodes when 4 | N) are
+# reproduced exactly by multilinear interpolation, and near the origin they are
+# linear: v(t, x) = V(t) x with V(t) = A + t B, [A, B] != 0.  There the exact
+# flow is linear, every interpolation the scheme makes is exact, and what is
+# left is the time discretisation of the characteristic alone.
+
+def _tri(x):
+    y = np.mod(x + 0.25, 1.0) - 0.25
+    return np.where(y <= 0.25, y, 0.5 - y)
+
+
+_A = np.array([[0.15, 0.45], [-0.35, -0.05]])
+_B = np.array([[0.30, -0.20], [0.40, 0.10]])
+_C = np.array([1.0, -0.7])          # I0 = C . tri(x)
+
+
+def _affine_case(N, Nt):
+    """(signed node coordinates (2, N, N), I0, velocity grids at t_n)."""
+    s = np.arange(N) / N
+    s = np.where(s < 0.5, s, s - 1.0)
+    X = np.stack(np.meshgrid(s, s, indexing="ij"))
+    T = _tri(X)
+    I0 = _C[0] * T[0] + _C[1] * T[1]
+    vg = [np.einsum("jk,k...->j...", _A + (n / Nt) * _B, T) for n in range(Nt + 1)]
+    return X, I0, vg
+
+
+def _flow_back(nsub=4000):
+    """Psi with Y(0) = Psi Y(1) for Y' = (A + t B) Y: classical RK4 on the 2x2
+    fundamental matrix from t = 1 down to t = 0."""
+    P = np.eye(2)
+    h = -1.0 / nsub
+    V = lambda t: _A + t * _B
+    t = 1.0
+    for _ in range(nsub):
+        k1 = V(t) @ P
+        k2 = V(t + 0.5 * h) @ (P + 0.5 * h * k1)
+        k3 = V(t + 0.5 * h) @ (P + 0.5 * h * k2)
+        k4 = V(t + h) @ (P + h * k3)
+        P = P + h / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+        t += h
+    return P
+
+
+def test_transport_characteristic_is_second_order_at_time_varying_velocity():
+    """m(1) against I0 at the exact inverse flow (a time-dependent linear flow
+    whose matrices do not commute): the error at the nodes near the origin falls
+    by 4 per halving of dt.  Evaluating v_n at the point reached with v_{n+1}
+    (the midpoint of the RK2 characteristic) is what makes the step second
+    order; evaluating both at x would fall by 2."""
+    N = 512
+    Psi = _flow_back()
+    errs = []
+    for Nt in (10, 20, 40):
+        X, I0, vg = _affine_case(N, Nt)
+        ms, _ = sweeps.transport(I0, vg, 1.0 / Nt)
+        inner = (np.abs(X[0]) <= 1.0 / 32) & (np.abs(X[1]) <= 1.0 / 32)
+        want = np.einsum("k,kj,j...->...", _C, Psi, X)
+        errs.append(np.abs(ms[-1] - want)[inner].max())
+    assert errs[-1] < 1e-5, errs
+    for r in (errs[0] / errs[1], errs[1] / errs[2]):
+        assert 3.6 < r < 4.4, errs
+
+
+def test_transport_foot_points_are_the_trapezoid_with_midpoint_velocity():
+    """Under the same exact interpolation each step's foot map is the matrix
+    I - dt/2 (V_{n+1} + V_n (I - dt V_{n+1})): v_{n+1} at the node, v_n at the
+    node moved back by dt v_{n+1} (the RK2 characteristic of the state equation).
+    m_Nt(x) = C . (X_0 X_1 ... X_{Nt-1}) x at the inner nodes to rounding; with
+    the roles of v_n and v_{n+1} exchanged the product differs by dt^3 [A, B]
+    per step."""
+    N, Nt = 256, 10
+    dt = 1.0 / Nt
+    X, I0, vg = _affine_case(N, Nt)
+    ms, feet = sweeps.transport(I0, vg, dt)
+    V = [_A + (n / Nt) * _B for n in range(Nt + 1)]
+    P = np.eye(2)
+    for n in range(Nt):
+        P = P @ (np.eye(2) - 0.5 * dt * (V[n + 1] + V[n] @ (np.eye(2) - dt * V[n + 1])))
+    inner = (np.abs(X[0]) <= 1.0 / 32) & (np.abs(X[1]) <= 1.0 / 32)
+    want = np.einsum("k,kj,j...->...", _C, P, X)
+    np.testing.assert_allclose(ms[-1][inner], want[inner], rtol=0, atol=1e-13)
+    # one step's foot points in index units, at every inner node
+    Xn = np.eye(2) - 0.5 * dt * (V[1] + V[0] @ (np.eye(2) - dt * V[1]))
+    want_feet = np.einsum("jk,k...->j...", Xn, X) * N
+    got = feet[0] - np.round(feet[0] / N) * N          # signed index coordinates
+    np.testing.assert_allclose(got[:, inner], want_feet[:, inner], rtol=0, atol=1e-10)
