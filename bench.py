@@ -1,18 +1,21 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 LDDMM library: GN Hessian-vector products per second.
 
-One step = one inexact Gauss-Newton-Krylov iteration of the hot path (gradient
-with forward shoot, transport and adjoint Jacobi sweep; 20 PCG iterations,
-each one GN Hessian-vector product; Armijo line search) on the 3D 64^3
-ellipsoid phantom, band 16^3, Nt = 10, FP32 with FP64 reductions.
-``value`` = Hessian-vector products per second over the timed steps, summed
-over ranks (each rank registers its own pair: weak scaling, no collective on
-the data path).
+One step = one whole inexact Gauss-Newton-Krylov solve of the hot path from
+v0 = 0: 10 GN iterations, each a gradient (forward shoot, transport, adjoint
+Jacobi sweep), 20 PCG iterations (one GN Hessian-vector product each) and an
+Armijo line search.  Default workload: the 160x192x160 brain phantom, band
+32^3, Nt = 10, FP32 with FP64 reductions and tcgen05 3xTF32 transforms (the
+largest single-GPU configuration); ``--workload 3d_64_ellipsoids`` runs the
+64^3 ellipsoid phantom, band 16^3.  ``value`` = Hessian-vector products per
+second over the timed steps, summed over ranks (each rank registers its own
+pair: weak scaling, no collective on the data path).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
-``--impl reference`` times the FP64 CPU oracle on the host cores (one
-Hessian-vector product per step at a fixed linearisation point).
+``--impl reference`` times the FP64 CPU oracle on the host cores: one
+Hessian-vector product per step at a fixed linearisation point, the steps
+spread over worker processes on all host cores.
 """
 
 import argparse
@@ -43,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="3d_64_ellipsoids")
+    ap.add_argument("--workload", default="3d_160x192x160_brain")
     ap.add_argument("--probe", default="auto", help="kernel class timed for the roofline (auto: dominant)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--state", default="image", choices=["image", "deformation"],
@@ -127,24 +130,71 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------- oracle
-def oracle_hessvec_rate(name, n_hv, seed_offset=0, state="image"):
-    """Hessian-vector products of the FP64 oracle per second (bounded sample)."""
-    import numpy as np
+# The FP64 oracle as it stands (single-threaded numpy/pocketfft), timed on the
+# host cores.  "All cores" runs independent copies of the same bounded sample in
+# worker processes (spawned: no CUDA state is inherited), one per core, and
+# counts the products all of them finish per second of wall time.
+ORACLE_MAX_WORKERS = 16
+
+
+def _oracle_problem(name, state):
     from oracle import deformation, objective
     from paper_1807_11560_gb300 import inputs
     kind, Ns, Ks, Nt, seed = workload(name)
-    I0, I1 = inputs.make_pair(kind, Ns, seed + seed_offset)
+    I0, I1 = inputs.make_pair(kind, Ns, seed)
     cls = deformation.DeformationProblem if state == "deformation" else objective.Problem
     P = cls(I0, I1, Ks, ALPHA, S, SIGMA, Nt)
     v0 = inputs.random_bl(Ks, len(Ns), seed + 1, 2.0, Ns)
-    lin = P.gradient(v0)
     p = inputs.random_bl(Ks, len(Ns), seed + 2, 1.0, Ns)
+    return P, v0, p
+
+
+def _oracle_worker(name, state, jobs, barrier, results):
+    """Linearise once (untimed, the worker's warm-up), wait for every worker,
+    then take Hessian-vector products from the shared job counter."""
+    P, v0, p = _oracle_problem(name, state)
+    lin = P.gradient(v0)
+    barrier.wait()
     times = []
-    for _ in range(n_hv):
+    while True:
+        with jobs.get_lock():
+            if jobs.value <= 0:
+                break
+            jobs.value -= 1
         t0 = time.perf_counter()
         P.hessvec(lin, p)
         times.append(time.perf_counter() - t0)
-    return times
+    results.put(times)
+
+
+def oracle_hessvec_rate(name, n_hv, state="image", workers=1):
+    """FP64 oracle Hessian-vector products at a fixed linearisation point:
+    n_hv products shared by `workers` processes.  Returns (products per second
+    of wall time, per-product times, wall seconds)."""
+    import multiprocessing as mp
+    for var in ("OMP_NUM_THREADS", "MKL_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        os.environ[var] = "1"
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers + 1)
+    jobs = ctx.Value("i", n_hv)
+    results = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(name, state, jobs, barrier, results))
+             for _ in range(workers)]
+    for q in procs:
+        q.start()
+    barrier.wait()
+    t0 = time.perf_counter()
+    times = []
+    for _ in procs:
+        times += results.get()
+    wall = time.perf_counter() - t0
+    for q in procs:
+        q.join()
+    return len(times) / wall, times, wall
+
+
+def oracle_workers(n):
+    return max(1, min(n, os.cpu_count() or 1, ORACLE_MAX_WORKERS))
 
 
 def run_reference(args):
@@ -153,21 +203,22 @@ def run_reference(args):
         return
     name = args.workload
     kind, Ns, Ks, Nt, seed = workload(name)
-    times = oracle_hessvec_rate(name, args.warmup + args.steps, state=args.state)[args.warmup:]
-    total = sum(times)
-    value = len(times) / total
+    workers = oracle_workers(args.steps)
+    value, times, wall = oracle_hessvec_rate(name, args.steps, state=args.state, workers=workers)
     sample = (f"{len(times)} GN Hessian-vector products of the FP64 NumPy oracle at a fixed "
-              f"linearisation point ({name}), one per step")
+              f"linearisation point ({name}), one per step, spread over {workers} worker processes "
+              "(one host core each; each worker's untimed linearisation is its warm-up)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": name, "grid": list(Ns), "band": list(Ks), "Nt": Nt, "gn_iters": N_GN_CONFIG,
                    "pcg_per_gn": N_PCG, "state": args.state, "l2": "oracle on host cores",
-                   "step": "one bounded sample: GN Hessian-vector products at a fixed linearisation point"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-                         "host_cores": os.cpu_count()},
+                   "step": "one bounded sample: one GN Hessian-vector product at a fixed linearisation point"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample,
+                         "host_cores": os.cpu_count(),
+                         "seconds_per_product_median": statistics.median(times)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -220,7 +271,14 @@ def measured_traffic(workload_name, cls):
 
 PROBE_CLASSES = ("sweep", "iota_ab", "cpw", "pi_ba", "inc_step", "transport", "iota_full", "pi_full", "deform")
 HBM_CLASSES = ("inc_step", "transport")
-SMS, FP32_LANES = 152, 128
+FP32_LANES = 128
+# nominal dense tensor rates of the GB300 (PFLOP/s): TF32 takes the measured
+# BF16 peak times their ratio, and the 3xTF32 split issues three TF32 MMAs per
+# product, so its peak in algorithmic flops is a third of that
+NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
+# kernel classes whose contractions run on tcgen05 (3xTF32) in the per-evaluation
+# launches of padded grids above 32^3 points (the default tensor-core setting)
+TENSOR_CLASSES = ("iota_ab",)
 
 
 def pick_dominant(ctx, v, n_pcg):
@@ -364,11 +422,21 @@ def run_gpu(args):
             wunit = "B"
         else:
             mhz = clk.get("sm_mhz") or 2070.0
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
             achieved = work / avg_s / 1e12
-            peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
-            roof = {"bound": "alu", "unit": "TFLOP/s",
-                    "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz "
-                                   "(median sampled SM clock); FP32 SIMT contraction"}
+            tf32 = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]) * NOMINAL_TF32_OVER_BF16
+            tensor = {"peak": tf32 / 3.0, "frac": achieved / (tf32 / 3.0),
+                      "peak_source": f"{src} BF16 dense peak x 1.1/2.25 (nominal TF32/BF16) / 3 "
+                                     f"(3xTF32: three TF32 MMAs per product; of {src})"}
+            if probe_cls in TENSOR_CLASSES:
+                peak = tensor["peak"]
+                roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": tensor["peak_source"]}
+            else:
+                peak = sms * FP32_LANES * 2 * mhz * 1e6 / 1e12
+                roof = {"bound": "alu", "unit": "TFLOP/s",
+                        "peak_source": f"derived: {sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz "
+                                       "(median sampled SM clock); FP32 SIMT contraction",
+                        "vs_tensor_3xtf32": tensor}
             wunit = "flop"
         roof.update({"kernel": probe_cls, "achieved": achieved, "peak": peak, "frac": achieved / peak,
                      "traffic": measured_traffic(name, probe_cls), "traffic_unit": "B per launch (ncu)",
@@ -380,11 +448,16 @@ def run_gpu(args):
             roof["class_ms_one_gn_iteration"] = class_ms
         cpu = None
         if not args.no_cpu_baseline:
-            times = oracle_hessvec_rate(name, 3, state=args.state)
-            cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{len(times)} GN Hessian-vector products of the FP64 NumPy oracle on {name} "
-                             "at a fixed linearisation point (single-threaded numpy/pocketfft)",
-                   "host_cores": os.cpu_count()}
+            one, t1, _ = oracle_hessvec_rate(name, 1, state=args.state, workers=1)
+            nw = oracle_workers(os.cpu_count() or 1)
+            allc, tall, _ = oracle_hessvec_rate(name, nw, state=args.state, workers=nw)
+            cpu = {"value": allc, "unit": UNIT, "cores": nw, "kind": "oracle",
+                   "sample": f"{nw} GN Hessian-vector products of the FP64 NumPy oracle on {name} at a "
+                             f"fixed linearisation point, one per worker process on {nw} host cores "
+                             "(single-threaded numpy/pocketfft each; linearisation untimed)",
+                   "host_cores": os.cpu_count(),
+                   "single_core": {"value": one, "cores": 1, "seconds_per_product": t1[0],
+                                   "sample": "one product in one process"}}
         nvox, nband = int(np.prod(Ns)), d * int(np.prod(Ks))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

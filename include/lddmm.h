@@ -122,6 +122,13 @@ typedef struct {
                            lddmm_batch_gn_solve and lddmm_transport follow Section 3.3;
                            lddmm_exact_gradient, lddmm_hessvec_newton, lddmm_transport_vjp
                            and newton = 1 are state-form only (LDDMM_EINVAL). */
+  int debug_stall;      /* test hook of the time-out path, 0 (default) off.  n > 0: the
+                           first grid barrier of every persistent sweep waits for one
+                           arrival more than the grid has (it never comes) and every
+                           bounded wait gives up after n polls, so the sweep returns
+                           early and the call reports LDDMM_ETIMEOUT (the context is
+                           unusable afterwards: destroy it).  No GPU fault or hang is
+                           involved: every wait stays bounded. */
 } lddmm_opts;
 
 /* Report of lddmm_gn_solve.  The per-iteration arrays are optional
@@ -252,6 +259,8 @@ int lddmm_iota(lddmm_ctx* ctx, const void* a, int ncomp, void* f_out);
  *   a              device pointer, complex64 [ncomp][K..], symmetrised on entry.
  *   ncomp          1..36 scalar fields.
  *   f_out          device pointer, float32 [ncomp][N..].
+ *   a and f_out must be memory of the current device (or managed memory);
+ *   the call cannot see their extents, so the caller guarantees the sizes.
  *   stream         cudaStream_t (NULL = legacy default stream).
  * The call is asynchronous: it returns once its kernels are enqueued.
  * It calls no cudaMalloc or cudaFree.  Its scratch is one fixed 32 MiB
@@ -261,7 +270,9 @@ int lddmm_iota(lddmm_ctx* ctx, const void* a, int ncomp, void* f_out);
  * (ncomp K1 K2 K3) and one intermediate (ncomp K1/2 N2 N3); if that exceeds
  * 32 MiB the call returns LDDMM_ENOMEM and does nothing (3 fields on
  * 160x192x160 with band 32^3 need about 13 MiB).  LDDMM_EINVAL for bad sizes
- * (as in lddmm_create) or for a or f_out not being device memory.
+ * (as in lddmm_create) or for a or f_out not being memory of the current
+ * device.  LDDMM_ECUDA without launching anything if a CUDA error of earlier
+ * work is pending on entry (it is left for the caller to read). 
  * The first call on each device performs a one-time set-up (it looks up the
  * device address of the scratch array); make that first call before any
  * stream capture.  All calls share the one array and it keeps the last

@@ -35,6 +35,7 @@
 
 struct lddmm_ctx {
   int precision;
+  int device;      // the CUDA device current at lddmm_create; every call runs on it
   void* impl;
   std::string err;
 };
@@ -641,7 +642,8 @@ struct Impl {
   void run_sweep(PwMode mode, const EvalDesc<T>* ev, int nev = 0) {
     if (nev == 0) nev = 2 * Nt;
     pb(PR_SWEEP);
-    cuda(sweep_launch<T>(pad, mode, ev, nev, Lhat, T2, P2, bar, dres + 7, st), "persistent sweep");
+    cuda(sweep_launch<T>(pad, mode, ev, nev, Lhat, T2, P2, bar, dres + 7, st, opts.debug_stall),
+         "persistent sweep");
     pe(PR_SWEEP, sweep_flops[mode] * nev / (2.0 * Nt));
     ++launches;
   }
@@ -1650,9 +1652,37 @@ int guarded(lddmm_ctx* ctx, F&& f) {
   }
 }
 
+// Makes the context's device current for the duration of one call (host
+// threads start on device 0, and a caller may have switched devices since the
+// context was created) and restores the caller's device afterwards.
+struct DeviceScope {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      ok = false;
+      return;
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) {
+      cudaGetLastError();
+      ok = false;
+    }
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
 template <typename Fn>
 int dispatch(lddmm_ctx* ctx, Fn&& fn) {
   if (!ctx) return LDDMM_EINVAL;
+  DeviceScope scope(ctx->device);
+  if (!scope.ok) {
+    ctx->err = "cannot make the context's device current";
+    return LDDMM_ECUDA;
+  }
   if (ctx->precision == LDDMM_FP64)
     return guarded(ctx, [&] { fn(*static_cast<Impl<double>*>(ctx->impl)); });
   return guarded(ctx, [&] { fn(*static_cast<Impl<float>*>(ctx->impl)); });
@@ -1686,6 +1716,7 @@ void lddmm_default_opts(lddmm_opts* o) {
   o->autotune = 1;
   o->newton = 0;
   o->state_eq = 0;
+  o->debug_stall = 0;
 }
 
 int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, double alpha, int s,
@@ -1707,9 +1738,16 @@ int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, doubl
   if (o.precision != LDDMM_FP32 && o.precision != LDDMM_FP64) return LDDMM_EINVAL;
   if (o.state_eq != 0 && o.state_eq != 1) return LDDMM_EINVAL;
   if (o.state_eq == 1 && o.newton != 0) return LDDMM_EINVAL;
+  if (o.debug_stall < 0) return LDDMM_EINVAL;
+  int device = -1;
+  if (cudaGetDevice(&device) != cudaSuccess) {
+    cudaGetLastError();
+    return LDDMM_ECUDA;
+  }
   lddmm_ctx* ctx = new (std::nothrow) lddmm_ctx();
   if (!ctx) return LDDMM_ENOMEM;
   ctx->precision = o.precision;
+  ctx->device = device;
   ctx->impl = nullptr;
   int rc;
   if (o.precision == LDDMM_FP64) {
@@ -1933,6 +1971,7 @@ const char* lddmm_last_error(const lddmm_ctx* ctx) {
 
 void lddmm_destroy(lddmm_ctx* ctx) {
   if (!ctx) return;
+  lddmm::DeviceScope scope(ctx->device);
   if (ctx->impl) {
     if (ctx->precision == LDDMM_FP64) {
       auto* im = static_cast<Impl<double>*>(ctx->impl);

@@ -166,11 +166,14 @@ struct EvalDesc {
 // (sweep.cu); ev is a device array of nev descriptors of one mode.  bar:
 // kSweepBarWords device unsigned ints of barrier state (the grid-barrier
 // arrival counter and one completion counter per (component, h) band slab);
-// flag: device double set to 1 if a wait gave up.
+// flag: device double set to 1 if a wait gave up.  stall > 0 is the test hook
+// of the time-out path: the first grid barrier then waits for one arrival more
+// than the grid has and every wait gives up after `stall` polls.
 constexpr int kSweepBarWords = 128;
 template <typename T>
 cudaError_t sweep_launch(const Plan<T>& p, PwMode mode, const EvalDesc<T>* ev, int nev, const T* Lhat,
-                         cplx<T>* T2, cplx<T>* P2, unsigned* bar, double* flag, cudaStream_t st);
+                         cplx<T>* T2, cplx<T>* P2, unsigned* bar, double* flag, cudaStream_t st,
+                         int stall = 0);
 
 // largest dynamic shared memory the transform kernels need on plan p when pi
 // batches hold up to nper_max fields per component and (brackets) bracket

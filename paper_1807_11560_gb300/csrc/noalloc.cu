@@ -63,13 +63,15 @@ __global__ void k_iota_twiddles(float2* E3f, float2* E2f, float2* E1f, Band b, D
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
-bool is_device_pointer(const void* p) {
+// device memory of device dev (or managed memory, which every device reaches)
+bool is_device_pointer(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -95,6 +97,9 @@ extern "C" int lddmm_iota_noalloc(int ndim, const int* grid, const int* K, const
                st2 = align256((size_t)ncomp * b.h1 * N.n2 * N.n3 * c8);
   if (s3 + s2 + s1 + sh + st2 > kNoAllocBytes) return LDDMM_ENOMEM;
 
+  // an error left pending by earlier work of the caller is not this call's:
+  // report it without launching anything (and leave it for the caller)
+  if (cudaPeekAtLastError() != cudaSuccess) return LDDMM_ECUDA;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
@@ -105,7 +110,7 @@ extern "C" int lddmm_iota_noalloc(int ndim, const int* grid, const int* K, const
     ds.err = cudaGetSymbolAddress(reinterpret_cast<void**>(&ds.ptr), g_noalloc_scratch);
   });
   if (ds.err != cudaSuccess || !ds.ptr) return LDDMM_ECUDA;
-  if (!is_device_pointer(a) || !is_device_pointer(f_out)) return LDDMM_EINVAL;
+  if (!is_device_pointer(a, dev) || !is_device_pointer(f_out, dev)) return LDDMM_EINVAL;
 
   unsigned char* base = ds.ptr;
   Plan<float> p{};
@@ -122,6 +127,7 @@ extern "C" int lddmm_iota_noalloc(int ndim, const int* grid, const int* K, const
   const long long ntw = (long long)b.k3 * N.n3 + (long long)b.k2 * N.n2 + (long long)b.h1 * N.n1;
   k_iota_twiddles<<<(unsigned)((ntw + 255) / 256), 256, 0, st>>>(p.E3f, p.E2f, p.E1f, b, N);
   hermitianize<float>(static_cast<const float2*>(a), herm, ncomp, b, st);
+  if (cudaGetLastError() != cudaSuccess) return LDDMM_ECUDA;   // nothing further is enqueued
   IotaDesc<float> d{};
   d.nf = ncomp;
   for (int c = 0; c < ncomp; ++c) {

@@ -37,6 +37,8 @@ struct SweepArgs {
   dev::BAGeom ba;             // geometry of the pi B'/A' phase
   unsigned* bar;              // [0] arrival counter, [1 + c H1 + h] slab completion counters
   double* flag;               // set to 1 when a barrier wait gives up
+  long long spin_limit;       // polls before a wait gives up
+  unsigned stall;             // test hook: arrivals the first barrier waits for beyond the grid
 };
 
 __device__ __forceinline__ unsigned load_acquire(const unsigned* p) {
@@ -48,16 +50,17 @@ __device__ __forceinline__ unsigned load_acquire(const unsigned* p) {
 // Grid-wide barrier on a monotonic arrival counter (zeroed before the launch):
 // the k-th barrier of the launch completes when the counter reaches
 // k * gridDim.x.  One atomic per CTA, then acquire loads until the target.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& target, double* flag) {
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& target, double* flag,
+                                             long long limit, unsigned extra = 0) {
   __syncthreads();
-  target += gridDim.x;
+  target += gridDim.x + extra;
   int ok = 1;
   if (threadIdx.x == 0) {
     __threadfence();
     atomicAdd(count, 1u);
     long long it = 0;
     while (load_acquire(count) < target) {
-      if (++it > kSpinLimit) {
+      if (++it > limit) {
         *(volatile double*)flag = 1.0;
         break;
       }
@@ -77,12 +80,12 @@ __device__ __forceinline__ void signal_slab(unsigned* cnt) {
 }
 
 // wait until a slab completion counter reaches target (acquire), bounded
-__device__ __forceinline__ bool wait_slab(const unsigned* cnt, unsigned target, double* flag) {
+__device__ __forceinline__ bool wait_slab(const unsigned* cnt, unsigned target, double* flag, long long limit) {
   int ok = 1;
   if (threadIdx.x == 0) {
     long long it = 0;
     while (load_acquire(cnt) < target) {
-      if (++it > kSpinLimit) {
+      if (++it > limit) {
         *(volatile double*)flag = 1.0;
         break;
       }
@@ -130,17 +133,19 @@ k_sweep(SweepArgs<T> a) {
     for (int vb = blockIdx.x; vb < n_ab; vb += gridDim.x) {
       const int f = vb / H1, h = vb % H1;
       const dev::FieldSpec<T> fs = dev::field24<T>(A, B, kvol, f);
-      if (ev > 0 && !wait_slab(a.bar + 1 + dev::field24_comp(f) * H1 + h, (unsigned)(a.ba.nch * ev), a.flag))
+      if (ev > 0 &&
+          !wait_slab(a.bar + 1 + dev::field24_comp(f) * H1 + h, (unsigned)(a.ba.nch * ev), a.flag, a.spin_limit))
         return;
       dev::phase_iota_ab<T, TWS>(p, fs, f, h, a.Lhat, a.T2, smraw);
       __syncthreads();
     }
-    if (!grid_barrier(a.bar, target, a.flag)) return;
+    // (the test hook makes the very first barrier wait for arrivals that never come)
+    if (!grid_barrier(a.bar, target, a.flag, a.spin_limit, ev == 0 ? a.stall : 0u)) return;
     for (int vb = blockIdx.x; vb < n_cpw; vb += gridDim.x) {
       dev::phase_cpw<T, MODE>(p, a.T2, slot, E->slot2, a.P2, a.TP, vb, smraw);
       __syncthreads();
     }
-    if (!grid_barrier(a.bar, target, a.flag)) return;
+    if (!grid_barrier(a.bar, target, a.flag, a.spin_limit)) return;
     for (int vb = blockIdx.x; vb < n_ba; vb += gridDim.x) {
       dev::phase_pi_ba<T>(p, E->epi, a.Lhat, a.P2, a.ba, vb, smraw);
       const int h = (vb / a.ba.nch) % H1, c = vb / (a.ba.nch * H1);
@@ -184,8 +189,10 @@ cudaError_t dispatch_tws(const SweepArgs<T>& a, size_t smem, bool tws, cudaStrea
 
 template <typename T>
 cudaError_t sweep_launch(const Plan<T>& p, PwMode mode, const EvalDesc<T>* ev, int nev, const T* Lhat,
-                         cplx<T>* T2, cplx<T>* P2, unsigned* bar, double* flag, cudaStream_t st) {
+                         cplx<T>* T2, cplx<T>* P2, unsigned* bar, double* flag, cudaStream_t st, int stall) {
   SweepArgs<T> a;
+  a.spin_limit = stall > 0 ? (long long)stall : kSpinLimit;
+  a.stall = stall > 0 ? 1u : 0u;
   a.p = p;
   a.Lhat = Lhat;
   a.T2 = T2;
@@ -216,9 +223,9 @@ cudaError_t sweep_launch(const Plan<T>& p, PwMode mode, const EvalDesc<T>* ev, i
 
 template cudaError_t sweep_launch<float>(const Plan<float>&, PwMode, const EvalDesc<float>*, int,
                                          const float*, cplx<float>*, cplx<float>*, unsigned*, double*,
-                                         cudaStream_t);
+                                         cudaStream_t, int);
 template cudaError_t sweep_launch<double>(const Plan<double>&, PwMode, const EvalDesc<double>*, int,
                                           const double*, cplx<double>*, cplx<double>*, unsigned*, double*,
-                                          cudaStream_t);
+                                          cudaStream_t, int);
 
 }  // namespace lddmm

@@ -33,7 +33,7 @@ class Opts(ctypes.Structure):
                 ("max_halvings", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("persistent", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("recompute", ctypes.c_int), ("autotune", ctypes.c_int), ("newton", ctypes.c_int),
-                ("state_eq", ctypes.c_int)]
+                ("state_eq", ctypes.c_int), ("debug_stall", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -160,8 +160,22 @@ def iota_noalloc(grid, K, a, ncomp, out, stream=None):
     device allocation (FP32; a and out must be CUDA tensors).  Asynchronous on
     ``stream``; returns the status code (0 = OK)."""
     grid, K = tuple(int(g) for g in grid), tuple(int(k) for k in K)
+    if len(grid) != len(K):
+        raise ValueError("grid and K need one size per axis each")
     if _dtype_name(a) != "complex64" or _dtype_name(out) != "float32":
         raise TypeError("iota_noalloc takes complex64 input and float32 output")
+    # the C entry point cannot see extents: an undersized array would be read or
+    # written out of bounds on the device, so the sizes are checked here
+    if int(np.prod(a.shape)) != int(ncomp) * int(np.prod(K)):
+        raise ValueError(f"a must hold ncomp * prod(K) = {int(ncomp) * int(np.prod(K))} values")
+    if int(np.prod(out.shape)) != int(ncomp) * int(np.prod(grid)):
+        raise ValueError(f"out must hold ncomp * prod(grid) = {int(ncomp) * int(np.prod(grid))} values")
+    import torch
+    if not (isinstance(a, torch.Tensor) and isinstance(out, torch.Tensor) and a.is_cuda and out.is_cuda):
+        raise TypeError("iota_noalloc takes CUDA tensors")
+    cur = torch.cuda.current_device()
+    if a.device.index != cur or out.device.index != cur:
+        raise ValueError("a and out must be on the current CUDA device")
     arr = ctypes.c_int * len(grid)
     return lib().lddmm_iota_noalloc(len(grid), arr(*grid), arr(*K), _ptr(a), int(ncomp), _ptr(out), stream)
 
@@ -177,7 +191,8 @@ class Context:
 
     def __init__(self, grid, K, alpha, s, sigma, Nt, precision="fp32", stream=None,
                  use_graphs=True, pcg_tol=1e-12, armijo_c=1e-4, max_halvings=10, persistent="auto",
-                 tensor_cores="auto", recompute=False, autotune=True, newton=False, state="image"):
+                 tensor_cores="auto", recompute=False, autotune=True, newton=False, state="image",
+                 debug_stall=0):
         L = lib()
         self.grid, self.K = tuple(int(g) for g in grid), tuple(int(k) for k in K)
         self.ndim = len(self.grid)
@@ -195,6 +210,7 @@ class Context:
         o.autotune = 1 if autotune else 0
         o.newton = 1 if newton else 0
         o.state_eq = {"image": 0, "deformation": 1}[state]
+        o.debug_stall = int(debug_stall)
         o.pcg_tol, o.armijo_c, o.max_halvings = pcg_tol, armijo_c, max_halvings
         arr = ctypes.c_int * self.ndim
         h = ctypes.c_void_p()
