@@ -54,12 +54,23 @@ def parse():
                          "state equation (Section 3.3)")
     ap.add_argument("--tensor-cores", default="auto", choices=["auto", "on", "off"],
                     help="image-grid band-to-grid transforms on tcgen05 (3xTF32): auto = grids >= 2^20 voxels")
+    ap.add_argument("--persistent", default="auto", choices=["auto", "on", "off"],
+                    help="band-limited sweeps as one persistent kernel: auto = padded grids up to 32^3")
+    ap.add_argument("--grid", default=None,
+                    help="override the workload's image grid, e.g. 64,64,64 (a smaller case of the same "
+                         "phantom and band, for kernel captures)")
+    ap.add_argument("--band", default=None, help="override the workload's band, e.g. 32,32,32")
     return ap.parse_args()
+
+
+SIZE_OVERRIDE = {}
 
 
 def workload(name):
     from paper_1807_11560_gb300 import inputs
     kind, Ns, Ks, Nt, seed = inputs.WORKLOADS[name]
+    Ns = SIZE_OVERRIDE.get("grid", Ns)
+    Ks = SIZE_OVERRIDE.get("band", Ks)
     return kind, Ns, Ks, Nt, seed
 
 
@@ -213,7 +224,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": name, "grid": list(Ns), "band": list(Ks), "Nt": Nt, "gn_iters": N_GN_CONFIG,
+        "config": {"workload": name if not SIZE_OVERRIDE else f"{name} resized", "grid": list(Ns),
+                   "band": list(Ks), "Nt": Nt, "gn_iters": N_GN_CONFIG,
                    "pcg_per_gn": N_PCG, "state": args.state, "l2": "oracle on host cores",
                    "step": "one bounded sample: one GN Hessian-vector product at a fixed linearisation point"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample,
@@ -315,7 +327,8 @@ def run_gpu(args):
     I0d = torch.as_tensor(I0, dtype=torch.float32, device=dev)
     I1d = torch.as_tensor(I1, dtype=torch.float32, device=dev)
     ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision="fp32",
-                  tensor_cores={"auto": "auto", "on": True, "off": False}[args.tensor_cores], state=args.state)
+                  tensor_cores={"auto": "auto", "on": True, "off": False}[args.tensor_cores], state=args.state,
+                  persistent={"auto": "auto", "on": True, "off": False}[args.persistent])
     ctx.set_images(I0d, I1d)
     v = torch.zeros((d,) + tuple(Ks), dtype=torch.complex64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -463,7 +476,8 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": name, "grid": list(Ns), "band": list(Ks), "Nt": Nt,
+            "config": {"workload": name if not SIZE_OVERRIDE else f"{name} resized", "grid": list(Ns),
+                       "band": list(Ks), "Nt": Nt,
                        "gn_iters": N_GN_CONFIG, "pcg_per_gn": N_PCG, "state": args.state,
                        "step": f"one GN-Krylov solve from v0 = 0: {N_GN_CONFIG} GN iterations (gradient, "
                                f"{N_PCG} PCG Hessvecs, Armijo)",
@@ -619,6 +633,10 @@ def run_band_sweep(args):
 
 def main():
     args = parse()
+    if args.grid:
+        SIZE_OVERRIDE["grid"] = tuple(int(x) for x in args.grid.split(","))
+    if args.band:
+        SIZE_OVERRIDE["band"] = tuple(int(x) for x in args.band.split(","))
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "population_32":

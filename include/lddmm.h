@@ -313,6 +313,19 @@ int lddmm_transport(lddmm_ctx* ctx, const void* v0, void* m1_out);
  * leaves it as the linearisation point. */
 int lddmm_transport_vjp(lddmm_ctx* ctx, const void* v0, const void* grad_m1, void* grad_v0_out);
 
+/* The same vector-Jacobian product through the exact discrete adjoint of the
+ * discretised map v0 -> m(1) (the route of Section 2.5, Eqs. 12-14, in discrete
+ * form, as in lddmm_exact_gradient): lambda(1) = grad_m1 is carried back through
+ * the transposes of the semi-Lagrangian steps, each time level's velocity
+ * sensitivity is projected to the band and the Heun shoot is transposed.  The
+ * result is the derivative of the discrete m(1) itself (central differences of
+ * the forward map converge to it), where lddmm_transport_vjp follows the
+ * paper's reduced adjoint Jacobi sweep.  Same arguments and output convention
+ * as lddmm_transport_vjp; needs opts.recompute = 0 and the image state form
+ * (LDDMM_EINVAL otherwise).  Atomic scatters make the rounding order vary from
+ * run to run.  Leaves v0 as the linearisation point. */
+int lddmm_transport_vjp_exact(lddmm_ctx* ctx, const void* v0, const void* grad_m1, void* grad_v0_out);
+
 /* dm(1) of the last lddmm_hessvec call (incremental state, Eq. 31). */
 int lddmm_last_dm1(lddmm_ctx* ctx, void* dm1_out);
 

@@ -219,7 +219,8 @@ class Problem:
         iteration counts and a flag telling whether the line search failed.
         """
         v = np.array(v0, dtype=np.complex128)
-        rep = {"E": [], "eps": [], "pcg_iters": [], "gnorm": [], "ls_failed": False}
+        rep = {"E": [], "eps": [], "pcg_iters": [], "gnorm": [], "ls_failed": False,
+               "v_hist": [], "trials": []}
         for _ in range(n_gn):
             lin = self.gradient(v)
             rep["E"].append(lin.E)
@@ -229,16 +230,20 @@ class Problem:
             slope = self.inner_V(lin.g, p)
             eps = 1.0
             accepted = False
+            trials = []                  # (eps, trial energy, Armijo bound) of each trial
             for _h in range(max_halvings + 1):
                 Et = self.energy(v + eps * p)
+                trials.append((eps, Et, lin.E + armijo_c * eps * slope))
                 if Et <= lin.E + armijo_c * eps * slope:
                     accepted = True
                     break
                 eps *= 0.5
+            rep["trials"].append(trials)
             if not accepted:
                 rep["ls_failed"] = True
                 break
             rep["eps"].append(eps)
             v = v + eps * p
+            rep["v_hist"].append(v.copy())
         rep["E_final"] = self.energy(v)
         return v, rep

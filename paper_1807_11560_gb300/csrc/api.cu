@@ -436,6 +436,13 @@ struct Impl {
         cuda(iota_ab_tc_twiddles(pad, tw, st), "tensor-core twiddles");
         pad.tc_ab = tw;
       }
+      // and those of the tcgen05 pi B'+A' of the same launches
+      if (opts.tensor_cores != 0 && pi_ba_tc_supported(pad)) {
+        float* tw = nullptr;
+        alloc(tw, pi_ba_tc_twiddle_floats(pad));
+        cuda(pi_ba_tc_twiddles(pad, tw, st), "tensor-core pi twiddles");
+        pad.tc_pi = tw;
+      }
     }
     if (opts.autotune && !persistent()) autotune();
     make_state(lin);                       // the cache layout follows the tile shapes
@@ -632,7 +639,7 @@ struct Impl {
     bracket_cpw<T>(pad, mode, T2, slot, slot2, P2, st);
     pe(PR_CPW, flops_cpw(mode));
     pb(PR_PI_BA);
-    bracket_pi<T>(pad, e, Lhat, P2, st);
+    bracket_pi<T>(pad, e, Lhat, P2, st, use_tc_pad() ? dres + 7 : nullptr);
     pe(PR_PI_BA, flops_pi_ba(e.nper));
     launches += kBracketLaunches;
     check_launch("bracket evaluation");
@@ -1112,6 +1119,24 @@ struct Impl {
   // in reverse time order).
   double exact_gradient_dev(const C* v0dev, C* gdev) {
     need_images();
+    exact_forward(v0dev);
+    energy_terms(lin);
+    // dE/dm(1) of the data term sigma^-2 h^d sum (m(1) - I1)^2
+    scaled_diff<T>(m1(lin), I1, 2.0 / (sigma * sigma * (double)Nvol), dm[0], Nvol, st);
+    ++launches;
+    exact_backward();
+    axpby<T>(gdev, 1.0, lin.vh, 1.0, W, 3 * Kvol, st);
+    ++launches;
+    check_launch("exact gradient");
+    const double E = read_energy();
+    have_lin = true;
+    have_dm1 = false;
+    have_zhist = false;
+    return E;
+  }
+
+  // forward sweep of lin at v0 with the histories the exact adjoint reads
+  void exact_forward(const C* v0dev) {
     if (opts.recompute) {
       *err = "the exact discrete adjoint reads the histories in reverse: create the context with recompute = 0";
       throw Fail{LDDMM_EINVAL};
@@ -1119,16 +1144,20 @@ struct Impl {
     cuda(cudaMemcpyAsync(lin.vh, v0dev, (size_t)3 * Kvol * sizeof(C), cudaMemcpyDeviceToDevice, st),
          "copy v0");
     forward(lin);
-    energy_terms(lin);
+  }
+
+  // reverse-mode sweep of the discrete map v0 -> m(1) from the cotangent
+  // lambda(1) = dL/dm(1) held in dm[0]: the transport reversed step by step,
+  // each level's velocity sensitivity projected to the band, the Heun shoot
+  // transposed; leaves the V-representer of dL/dv0 in W
+  void exact_backward() {
     T* lam_next = dm[0];
     T* lam_cur = dm[1];
     T* Gn = dvgrid;                       // G[n+1]
     T* Gc = dvgrid + 3 * Nvol;            // G[n]
     const size_t gbytes = (size_t)3 * Nvol * sizeof(T);
-    scaled_diff<T>(m1(lin), I1, 2.0 / (sigma * sigma * (double)Nvol), lam_next, Nvol, st);
     cuda(cudaMemsetAsync(Gn, 0, gbytes, st), "memset");
     cuda(cudaMemsetAsync(Gc, 0, gbytes, st), "memset");
-    ++launches;
     for (int n = Nt - 1; n >= 0; --n) {
       cuda(cudaMemsetAsync(lam_cur, 0, (size_t)Nvol * sizeof(T), st), "memset");
       adjoint_step<T>(lam_next, mstate(lin, n), vgr(lin, n), vgr(lin, n + 1), offp(lin, n), lam_cur, Gn, Gc,
@@ -1141,14 +1170,7 @@ struct Impl {
     }
     project_adjoint(Gn, srcs);
     backward_sources(lin);
-    axpby<T>(gdev, 1.0, lin.vh, 1.0, W, 3 * Kvol, st);
-    ++launches;
-    check_launch("exact gradient");
-    const double E = read_energy();
-    have_lin = true;
-    have_dm1 = false;
-    have_zhist = false;
-    return E;
+    check_launch("exact adjoint sweep");
   }
 
   // enqueue one GN Hessian-vector product: input dvh[0], output vout
@@ -1625,6 +1647,28 @@ struct Impl {
     have_dm1 = false;
   }
 
+  // the same vector-Jacobian product through the exact discrete adjoint of the
+  // discretised map (the transposes of the semi-Lagrangian steps and of the Heun
+  // shoot): the derivative of the discrete m(1) itself
+  void transport_vjp_exact(const void* v0, const void* gm1, void* out) {
+    state_form_only("lddmm_transport_vjp_exact");
+    need_images();
+    load_bl(v0, vsol);
+    exact_forward(vsol);
+    cuda(cudaMemcpyAsync(dm[0], gm1, (size_t)Nvol * sizeof(T), cudaMemcpyDefault, st), "copy grad m1");
+    exact_backward();
+    scale_L<T>(gbuf, W, Lhat, 3, Kvol, st);
+    ++launches;
+    check_launch("exact transport vjp");
+    store_bl(gbuf, out);
+    cuda(cudaMemcpyAsync(hres + 7, dres + 7, sizeof(double), cudaMemcpyDeviceToHost, st), "read flag");
+    sync("exact transport vjp");
+    check_flag(hres[7]);
+    have_lin = true;
+    have_zhist = false;
+    have_dm1 = false;
+  }
+
   void last_dm1(void* out) {
     if (!have_dm1) {
       *err = "no Hessian-vector product computed at this linearisation point";
@@ -1906,6 +1950,13 @@ int lddmm_transport_vjp(lddmm_ctx* ctx, const void* v0, const void* grad_m1, voi
   if (bad_ptr(ctx, v0, "v0") || bad_ptr(ctx, grad_m1, "grad_m1") || bad_ptr(ctx, grad_v0, "grad_v0_out"))
     return LDDMM_EINVAL;
   return lddmm::dispatch(ctx, [&](auto& im) { im.transport_vjp(v0, grad_m1, grad_v0); });
+}
+
+int lddmm_transport_vjp_exact(lddmm_ctx* ctx, const void* v0, const void* grad_m1, void* grad_v0) {
+  if (!ctx) return LDDMM_EINVAL;
+  if (bad_ptr(ctx, v0, "v0") || bad_ptr(ctx, grad_m1, "grad_m1") || bad_ptr(ctx, grad_v0, "grad_v0_out"))
+    return LDDMM_EINVAL;
+  return lddmm::dispatch(ctx, [&](auto& im) { im.transport_vjp_exact(v0, grad_m1, grad_v0); });
 }
 
 int lddmm_last_dm1(lddmm_ctx* ctx, void* out) {

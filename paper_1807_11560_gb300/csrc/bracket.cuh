@@ -27,6 +27,15 @@ constexpr int kAccB = 2;      // B' columns per thread in phase_pi_ba (nper * G3
 constexpr int kRed = 8;       // threads sharing one A' sum in phase_pi_ba
 
 __host__ __device__ __forceinline__ int sfreq(int q, int K) { return (2 * q < K) ? q : q - K; }
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while its predecessor runs; it stages its constant
+// operands (twiddles, symbols) first and waits here before touching anything
+// an earlier kernel wrote.  Without that launch attribute (and inside the
+// persistent sweep) the wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// lets the next kernel of the stream be scheduled (it still waits in pdl_wait)
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __host__ __device__ __forceinline__ bool nyq(int q, int K) { return (K % 2 == 0) && (2 * q == K); }
 
 template <typename C>
@@ -167,6 +176,7 @@ __device__ __forceinline__ void phase_iota_ab(const Plan<T>& p, const FieldSpec<
   }
   const C* __restrict__ src = fs.src + (long long)h * K2 * K3;
   const T* __restrict__ Lrow = Lhat + (long long)h * K2 * K3;
+  pdl_wait();
   cp_async_run(S0, src, K2 * K3);
   if (fs.applyL) cp_async_run(sL, Lrow, K2 * K3);
   cp_async_wait_all();
@@ -263,6 +273,20 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
   const long long p0 = (long long)vb * TP;
   const C zero{T(0), T(0)};
 
+  if (p.E1fp != nullptr) {                                 // constant operands first
+    cp_async_run(sE1f, p.E1fp, H1 * G1q);
+    cp_async_run(sE1b, p.E1bp, G1 * H1q);
+  } else {
+    for (int i = tid; i < H1 * G1q; i += kThreads) {
+      const int h = i / G1q, x = i - h * G1q;
+      if (x < G1) cp_async(sE1f + i, p.E1f + h * G1 + x); else sE1f[i] = zero;
+    }
+    for (int i = tid; i < G1 * H1q; i += kThreads) {
+      const int x = i / H1q, h = i - x * H1q;
+      if (h < H1) cp_async(sE1b + i, p.E1b + x * H1 + h); else sE1b[i] = zero;
+    }
+  }
+  pdl_wait();
   for (int fh = tid / TP, pp = tid - (tid / TP) * TP; fh < 24 * H1;) {
     if (p0 + pp < P) cp_async(sT2 + fh * TP + pp, T2 + (long long)fh * P + p0 + pp);
     else sT2[fh * TP + pp] = zero;
@@ -290,19 +314,6 @@ __device__ __forceinline__ void phase_cpw(const Plan<T>& p, const cplx<T>* __res
         cv[r][f] = ok ? cs[f * G1 * TP] : T(0);
         cl[r][f] = ok ? cs[(12 + f) * G1 * TP] : T(0);
       }
-    }
-  }
-  if (p.E1fp != nullptr) {
-    cp_async_run(sE1f, p.E1fp, H1 * G1q);
-    cp_async_run(sE1b, p.E1bp, G1 * H1q);
-  } else {
-    for (int i = tid; i < H1 * G1q; i += kThreads) {
-      const int h = i / G1q, x = i - h * G1q;
-      if (x < G1) cp_async(sE1f + i, p.E1f + h * G1 + x); else sE1f[i] = zero;
-    }
-    for (int i = tid; i < G1 * H1q; i += kThreads) {
-      const int x = i / H1q, h = i - x * H1q;
-      if (h < H1) cp_async(sE1b + i, p.E1b + x * H1 + h); else sE1b[i] = zero;
     }
   }
   cp_async_wait_all();
@@ -460,6 +471,11 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
       cp_async(E3s + k * G3s + x, p.E3b + i);
     }
   }
+  for (int it = tid; it < nslot; it += kThreads) {
+    const int kk = it / K3, k3 = it - kk * K3;
+    cp_async(sLh + it, Lhat + ((long long)h * K2 + kb + kk) * K3 + k3);
+  }
+  pdl_wait();
   for (int i = tid; i < nslot * kEpiX; i += kThreads) {
     const int jq = i / nslot, it = i - jq * nslot;
     const int j = jq / kMaxX, q = jq - j * kMaxX;
@@ -468,10 +484,6 @@ __device__ __forceinline__ void phase_pi_ba(const Plan<T>& p, const PiEpi<T>& e,
       const long long at = (long long)c * kvol + ((long long)h * K2 + kb + kk) * K3 + k3;
       cp_async(sX + jq * NS + it, e.X[j][q] + at);
     }
-  }
-  for (int it = tid; it < nslot; it += kThreads) {
-    const int kk = it / K3, k3 = it - kk * K3;
-    cp_async(sLh + it, Lhat + ((long long)h * K2 + kb + kk) * K3 + k3);
   }
 
   C acc[kAccB][kMaxKC];

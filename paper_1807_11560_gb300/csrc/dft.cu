@@ -23,6 +23,8 @@
 //   k_pi_C     CTA per (field, 256 pencils): C' of image-grid fields -> P2,
 //              each pencil streamed once.
 //   k_pi_BA    CTA per (component, h, k2 chunk): B', A', epilogue.
+#include <utility>
+
 #include "bracket.cuh"
 
 namespace lddmm {
@@ -42,10 +44,32 @@ void allow_smem() {
   (void)done;
 }
 
+// Launch with programmatic stream serialisation: the kernel may be scheduled
+// while the previous kernel of the stream still runs (its phase body waits in
+// pdl_wait before reading what earlier kernels wrote).  Used for the chain of
+// bracket-evaluation kernels, whose prologues (twiddle staging) then overlap
+// the tail of the kernel before.  Recorded as programmatic edges when the
+// stream is captured into a graph.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), unsigned grid, size_t smem, cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = kUsePdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 template <typename T, bool TWS>
 __global__ void __launch_bounds__(kThreads)
 k_iota_AB(Plan<T> p, IotaDesc<T> d, const T* __restrict__ Lhat, cplx<T>* __restrict__ T2) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  dev::pdl_trigger();
   const int f = blockIdx.x / p.b.h1, h = blockIdx.x % p.b.h1;
   const dev::FieldSpec<T> fs{d.src[f], d.deriv[f], d.applyL[f] != 0};
   dev::phase_iota_ab<T, TWS>(p, fs, f, h, Lhat, T2, smraw);
@@ -56,6 +80,7 @@ __global__ void __launch_bounds__(kThreads)
 k_cpw(Plan<T> p, const cplx<T>* __restrict__ T2, T* __restrict__ slot, T* __restrict__ slot2,
       cplx<T>* __restrict__ P2, int TP) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  dev::pdl_trigger();
   dev::phase_cpw<T, MODE>(p, T2, slot, slot2, P2, TP, blockIdx.x, smraw);
 }
 
@@ -63,6 +88,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_pi_BA(Plan<T> p, PiEpi<T> e, const T* __restrict__ Lhat, const cplx<T>* __restrict__ P2, dev::BAGeom g) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  dev::pdl_trigger();
   dev::phase_pi_ba<T>(p, e, Lhat, P2, g, blockIdx.x, smraw);
 }
 
@@ -144,21 +170,29 @@ k_pi_C(Plan<T> p, PiSrc<T> s, cplx<T>* __restrict__ P2) {
 }
 
 template <typename T>
-void launch_iota_AB(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2, cudaStream_t st) {
+void launch_iota_AB(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2, cudaStream_t st,
+                    bool pdl = false) {
+  const unsigned grid = (unsigned)(d.nf * p.b.h1);
   if (dev::ab_tws(p)) {
     allow_smem<k_iota_AB<T, true>>();
-    k_iota_AB<T, true><<<d.nf * p.b.h1, kThreads, dev::ab_smem(p, true), st>>>(p, d, Lhat, T2);
+    if (pdl) launch_pdl(k_iota_AB<T, true>, grid, dev::ab_smem(p, true), st, p, d, Lhat, T2);
+    else k_iota_AB<T, true><<<grid, kThreads, dev::ab_smem(p, true), st>>>(p, d, Lhat, T2);
   } else {
     allow_smem<k_iota_AB<T, false>>();
-    k_iota_AB<T, false><<<d.nf * p.b.h1, kThreads, dev::ab_smem(p, false), st>>>(p, d, Lhat, T2);
+    if (pdl) launch_pdl(k_iota_AB<T, false>, grid, dev::ab_smem(p, false), st, p, d, Lhat, T2);
+    else k_iota_AB<T, false><<<grid, kThreads, dev::ab_smem(p, false), st>>>(p, d, Lhat, T2);
   }
 }
 
 template <typename T>
-void launch_pi_BA(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T>* P2, cudaStream_t st) {
+void launch_pi_BA(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T>* P2, cudaStream_t st,
+                  bool pdl = false) {
   const dev::BAGeom g = dev::ba_geom(p, e.ncomp, e.nper);
+  const unsigned grid = (unsigned)(e.ncomp * p.b.h1 * g.nch);
+  const size_t smem = dev::ba_smem(p, e.nper, g);
   allow_smem<k_pi_BA<T>>();
-  k_pi_BA<T><<<e.ncomp * p.b.h1 * g.nch, kThreads, dev::ba_smem(p, e.nper, g), st>>>(p, e, Lhat, P2, g);
+  if (pdl) launch_pdl(k_pi_BA<T>, grid, smem, st, p, e, Lhat, P2, g);
+  else k_pi_BA<T><<<grid, kThreads, smem, st>>>(p, e, Lhat, P2, g);
 }
 
 }  // namespace
@@ -280,7 +314,7 @@ template <typename T>
 void bracket_iota(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2, cudaStream_t st,
                   double* tc_flag) {
   if (try_ab_tc<T>(p, d, Lhat, T2, tc_flag, st)) return;
-  launch_iota_AB<T>(p, d, Lhat, T2, st);
+  launch_iota_AB<T>(p, d, Lhat, T2, st, true);
 }
 
 template <typename T>
@@ -294,22 +328,37 @@ void bracket_cpw(const Plan<T>& p, PwMode mode, const cplx<T>* T2, T* slot, T* s
   switch (mode) {
     case PW_F:
       allow_smem<k_cpw<T, PW_F>>();
-      k_cpw<T, PW_F><<<grid, kThreads, smem, st>>>(p, T2, slot, slot2, P2, TP);
+      launch_pdl(k_cpw<T, PW_F>, grid, smem, st, p, T2, slot, slot2, P2, TP);
       break;
     case PW_T:
       allow_smem<k_cpw<T, PW_T>>();
-      k_cpw<T, PW_T><<<grid, kThreads, smem, st>>>(p, T2, slot, slot2, P2, TP);
+      launch_pdl(k_cpw<T, PW_T>, grid, smem, st, p, T2, slot, slot2, P2, TP);
       break;
     case PW_GT:
       allow_smem<k_cpw<T, PW_GT>>();
-      k_cpw<T, PW_GT><<<grid, kThreads, smem, st>>>(p, T2, slot, slot2, P2, TP);
+      launch_pdl(k_cpw<T, PW_GT>, grid, smem, st, p, T2, slot, slot2, P2, TP);
       break;
   }
 }
 
 template <typename T>
-void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T>* P2, cudaStream_t st) {
-  launch_pi_BA<T>(p, e, Lhat, P2, st);
+bool try_pi_tc(const Plan<T>&, const PiEpi<T>&, const T*, const cplx<T>*, double*, cudaStream_t) {
+  return false;
+}
+template <>
+bool try_pi_tc<float>(const Plan<float>& p, const PiEpi<float>& e, const float* Lhat, const float2* P2,
+                      double* flag, cudaStream_t st) {
+  if (!flag || p.tc_pi == nullptr) return false;
+  if (pi_ba_tc(p, e, Lhat, P2, flag, st) == cudaSuccess) return true;
+  cudaGetLastError();   // a refused launch configuration: the SIMT kernel runs instead
+  return false;
+}
+
+template <typename T>
+void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T>* P2, cudaStream_t st,
+                double* tc_flag) {
+  if (try_pi_tc<T>(p, e, Lhat, P2, tc_flag, st)) return;
+  launch_pi_BA<T>(p, e, Lhat, P2, st, true);
 }
 
 #define LDDMM_DFT_INST(T)                                                                          \
@@ -324,7 +373,7 @@ void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T
                             cudaStream_t);                                                         \
   template void bracket_iota<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t, double*); \
   template void bracket_cpw<T>(const Plan<T>&, PwMode, const cplx<T>*, T*, T*, cplx<T>*, cudaStream_t); \
-  template void bracket_pi<T>(const Plan<T>&, const PiEpi<T>&, const T*, const cplx<T>*, cudaStream_t);
+  template void bracket_pi<T>(const Plan<T>&, const PiEpi<T>&, const T*, const cplx<T>*, cudaStream_t, double*);
 LDDMM_DFT_INST(float)
 LDDMM_DFT_INST(double)
 

@@ -11,6 +11,15 @@
 
 namespace lddmm {
 
+// The kernels of a bracket evaluation launch with programmatic dependent
+// launch (their prologues overlap the previous kernel); building with
+// -DLDDMM_NO_PDL launches them plainly (same results, for comparison).
+#ifdef LDDMM_NO_PDL
+constexpr bool kUsePdl = false;
+#else
+constexpr bool kUsePdl = true;
+#endif
+
 template <typename T> struct CplxOf;
 template <> struct CplxOf<float> { using type = float2; };
 template <> struct CplxOf<double> { using type = double2; };
@@ -55,6 +64,9 @@ struct Plan {
   // FP32 padded plans: the tcgen05 iota A+B twiddle operands, expanded once
   // into the kernel's shared-memory layout (nullptr: expanded in the kernel)
   const float* tc_ab = nullptr;
+  // FP32 padded plans: the tcgen05 pi B'+A' twiddle operands (real form, hi/lo,
+  // in the kernel's shared-memory layout); nullptr: the SIMT kernel runs
+  const float* tc_pi = nullptr;
   // the twiddle tiles exactly as the phase bodies stage them in shared memory
   // (zero padded / transposed), so a phase copies them contiguously; nullptr:
   // the phases build the tiles from the tables above
@@ -126,6 +138,12 @@ cudaError_t iota_ab_tc(const Plan<float>& p, const IotaDesc<float>& d, const flo
                        double* flag, cudaStream_t st);
 cudaError_t iota_C_tc(const Plan<float>& p, const IotaDesc<float>& d, const float2* T2, double* flag,
                       cudaStream_t st);
+// tcgen05 pi stages B' + A' with the epilogue on a padded-grid bracket block (tc_pi.cu)
+bool pi_ba_tc_supported(const Plan<float>& p);
+size_t pi_ba_tc_twiddle_floats(const Plan<float>& p);
+cudaError_t pi_ba_tc_twiddles(const Plan<float>& p, float* dst, cudaStream_t st);
+cudaError_t pi_ba_tc(const Plan<float>& p, const PiEpi<float>& e, const float* Lhat, const float2* P2,
+                     double* flag, cudaStream_t st);
 template <typename T>
 void pi_batch(const Plan<T>& p, const PiSrc<T>& s, const PiEpi<T>& e, const T* Lhat,
               cplx<T>* P2, cudaStream_t st);
@@ -149,9 +167,10 @@ void bracket_iota(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>
 template <typename T>
 void bracket_cpw(const Plan<T>& p, PwMode mode, const cplx<T>* T2, T* slot, T* slot2, cplx<T>* P2,
                  cudaStream_t st);
+// tc_flag != nullptr selects the tcgen05 form (FP32 plans with p.tc_pi set)
 template <typename T>
 void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T>* P2,
-                cudaStream_t st);
+                cudaStream_t st, double* tc_flag = nullptr);
 // One bracket evaluation of a persistent sweep: iota sources (value/Jacobian
 // block from srcA, L~ block from srcB), stage-point slot and pi epilogue.
 template <typename T>

@@ -106,6 +106,9 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nslab = d.nf * H1;
   const int nitems = (nslab + g.S - 1) / g.S;
+  // programmatic dependent launch: let the next kernel be scheduled; the
+  // prologue below reads constants only, the wait precedes the band slabs
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   // twiddle operands, once per CTA: each complex twiddle fills a 2 x 2 block
   // of its real form
@@ -164,6 +167,7 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = *tslot;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   const uint32_t idA = idesc_tf32(kMTile, g.NA), idB = idesc_tf32(kMTile, g.NB);
   const uint32_t sboA = (uint32_t)(g.KA >> 2) * 128, sboB = (uint32_t)(g.KB >> 2) * 128;
@@ -387,7 +391,19 @@ cudaError_t launch_ab_tc(const Plan<float>& p, const IotaDesc<float>& d, const f
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const int nitems = (d.nf * p.b.h1 + g.S - 1) / g.S;
   const unsigned grid = (unsigned)std::min(nitems, sms);
-  kern<<<grid, kThr, smem, st>>>(p, d, Lhat, T2, g, flag);
+  // programmatic stream serialisation: the prologue (twiddle copy, TMEM
+  // allocation) overlaps the tail of the previous kernel
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThr);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = kUsePdl ? 1 : 0;
+  if ((e = cudaLaunchKernelEx(&cfg, kern, p, d, Lhat, T2, g, flag)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -120,6 +120,7 @@ def lib():
         "lddmm_transport": (I, [P, P, P]),
         "lddmm_last_dm1": (I, [P, P]),
         "lddmm_transport_vjp": (I, [P, P, P, P]),
+        "lddmm_transport_vjp_exact": (I, [P, P, P, P]),
         "lddmm_kernel_count": (ctypes.c_longlong, [P]),
         "lddmm_device_bytes": (ctypes.c_ulonglong, [P]),
         "lddmm_tile_config": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
@@ -324,10 +325,12 @@ class Context:
         self._check(lib().lddmm_transport(self._h, self._arg(v0, "cplx", self.nband),
                                           self._arg(m1_out, "real", self.nvox)))
 
-    def transport_vjp(self, v0, grad_m1, out):
-        self._check(lib().lddmm_transport_vjp(self._h, self._arg(v0, "cplx", self.nband),
-                                              self._arg(grad_m1, "real", self.nvox),
-                                              self._arg(out, "cplx", self.nband)))
+    def transport_vjp(self, v0, grad_m1, out, exact=False):
+        """l2 gradient of a loss of m(1) in v0 from dL/dm(1): the paper's adjoint
+        Jacobi sweep, or (exact=True) the exact discrete adjoint of the map."""
+        fn = lib().lddmm_transport_vjp_exact if exact else lib().lddmm_transport_vjp
+        self._check(fn(self._h, self._arg(v0, "cplx", self.nband), self._arg(grad_m1, "real", self.nvox),
+                       self._arg(out, "cplx", self.nband)))
 
     def last_dm1(self, out):
         self._check(lib().lddmm_last_dm1(self._h, self._arg(out, "real", self.nvox)))
