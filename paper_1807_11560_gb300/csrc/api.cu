@@ -306,15 +306,17 @@ struct Impl {
         if (t < best) { best = t; pick = tws; }
       }
       pad.tws = pick;
-      best = 1e30f;
-      pick = 0;
-      for (int tp : kTp) {
-        if (!tile_valid<T>(pad, pad.tws, tp, 0)) continue;
-        pad.tp = tp;
-        const float t = best_of([&] { bracket_cpw<T>(pad, PW_GT, T2, slot, nullptr, P2, st); });
-        if (t < best) { best = t; pick = tp; }
+      if (pad.tc_cpw == nullptr) {   // the tensor-core middle phase fixes its own tile
+        best = 1e30f;
+        pick = 0;
+        for (int tp : kTp) {
+          if (!tile_valid<T>(pad, pad.tws, tp, 0)) continue;
+          pad.tp = tp;
+          const float t = best_of([&] { bracket_cpw<T>(pad, PW_GT, T2, slot, nullptr, P2, st); });
+          if (t < best) { best = t; pick = tp; }
+        }
+        pad.tp = pick;
       }
-      pad.tp = pick;
       PiEpi<T> e = epi(3, 3);
       for (int o = 0; o < 3; ++o) {
         e.grp[o] = 0;
@@ -442,6 +444,14 @@ struct Impl {
         alloc(tw, pi_ba_tc_twiddle_floats(pad));
         cuda(pi_ba_tc_twiddles(pad, tw, st), "tensor-core pi twiddles");
         pad.tc_pi = tw;
+      }
+      // and of the tcgen05 C / products / C' (its tile fixes the cache layout)
+      if (use_tc_pad() && cpw_tc_supported(pad) && tile_valid<T>(pad, 0, cpw_tc_tile(), 0)) {
+        float* tw = nullptr;
+        alloc(tw, cpw_tc_twiddle_floats(pad));
+        cuda(cpw_tc_twiddles(pad, tw, st), "tensor-core cpw twiddles");
+        pad.tc_cpw = tw;
+        pad.tp = cpw_tc_tile();
       }
     }
     if (opts.autotune && !persistent()) autotune();
@@ -636,7 +646,7 @@ struct Impl {
     bracket_iota<T>(pad, block24(srcA, srcB, slot), Lhat, T2, st, use_tc_pad() ? dres + 7 : nullptr);
     pe(PR_IOTA_AB, flops_iota_ab());
     pb(PR_CPW);
-    bracket_cpw<T>(pad, mode, T2, slot, slot2, P2, st);
+    bracket_cpw<T>(pad, mode, T2, slot, slot2, P2, st, use_tc_pad() ? dres + 7 : nullptr);
     pe(PR_CPW, flops_cpw(mode));
     pb(PR_PI_BA);
     bracket_pi<T>(pad, e, Lhat, P2, st, use_tc_pad() ? dres + 7 : nullptr);

@@ -318,8 +318,22 @@ void bracket_iota(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>
 }
 
 template <typename T>
+bool try_cpw_tc(const Plan<T>&, PwMode, const cplx<T>*, T*, T*, cplx<T>*, double*, cudaStream_t) {
+  return false;
+}
+template <>
+bool try_cpw_tc<float>(const Plan<float>& p, PwMode mode, const float2* T2, float* slot, float* slot2,
+                       float2* P2, double* flag, cudaStream_t st) {
+  if (!flag || p.tc_cpw == nullptr) return false;
+  if (cpw_tc(p, mode, T2, slot, slot2, P2, flag, st) == cudaSuccess) return true;
+  cudaGetLastError();   // a refused launch configuration: the SIMT kernel runs instead
+  return false;
+}
+
+template <typename T>
 void bracket_cpw(const Plan<T>& p, PwMode mode, const cplx<T>* T2, T* slot, T* slot2, cplx<T>* P2,
-                 cudaStream_t st) {
+                 cudaStream_t st, double* tc_flag) {
+  if (try_cpw_tc<T>(p, mode, T2, slot, slot2, P2, tc_flag, st)) return;
   const int TP = dev::cpw_tile(p);
   const int NP = (mode == PW_GT) ? 9 : 3;
   const size_t smem = dev::cpw_smem(p, TP, NP);
@@ -372,7 +386,7 @@ void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T
   template void pi_batch<T>(const Plan<T>&, const PiSrc<T>&, const PiEpi<T>&, const T*, cplx<T>*,  \
                             cudaStream_t);                                                         \
   template void bracket_iota<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t, double*); \
-  template void bracket_cpw<T>(const Plan<T>&, PwMode, const cplx<T>*, T*, T*, cplx<T>*, cudaStream_t); \
+  template void bracket_cpw<T>(const Plan<T>&, PwMode, const cplx<T>*, T*, T*, cplx<T>*, cudaStream_t, double*); \
   template void bracket_pi<T>(const Plan<T>&, const PiEpi<T>&, const T*, const cplx<T>*, cudaStream_t, double*);
 LDDMM_DFT_INST(float)
 LDDMM_DFT_INST(double)

@@ -67,6 +67,9 @@ struct Plan {
   // FP32 padded plans: the tcgen05 pi B'+A' twiddle operands (real form, hi/lo,
   // in the kernel's shared-memory layout); nullptr: the SIMT kernel runs
   const float* tc_pi = nullptr;
+  // FP32 padded plans: the tcgen05 C / C' twiddle operands of the middle phase
+  // (tc_cpw.cu); with them set, tp is the tensor-core tile (8 pencils)
+  const float* tc_cpw = nullptr;
   // the twiddle tiles exactly as the phase bodies stage them in shared memory
   // (zero padded / transposed), so a phase copies them contiguously; nullptr:
   // the phases build the tiles from the tables above
@@ -138,6 +141,14 @@ cudaError_t iota_ab_tc(const Plan<float>& p, const IotaDesc<float>& d, const flo
                        double* flag, cudaStream_t st);
 cudaError_t iota_C_tc(const Plan<float>& p, const IotaDesc<float>& d, const float2* T2, double* flag,
                       cudaStream_t st);
+// tcgen05 C + bracket products + C' of a padded-grid bracket block (tc_cpw.cu)
+enum PwMode : int;
+bool cpw_tc_supported(const Plan<float>& p);
+int cpw_tc_tile();
+size_t cpw_tc_twiddle_floats(const Plan<float>& p);
+cudaError_t cpw_tc_twiddles(const Plan<float>& p, float* dst, cudaStream_t st);
+cudaError_t cpw_tc(const Plan<float>& p, PwMode mode, const float2* T2, float* slot, float* slot2, float2* P2,
+                   double* flag, cudaStream_t st);
 // tcgen05 pi stages B' + A' with the epilogue on a padded-grid bracket block (tc_pi.cu)
 bool pi_ba_tc_supported(const Plan<float>& p);
 size_t pi_ba_tc_twiddle_floats(const Plan<float>& p);
@@ -150,7 +161,7 @@ void pi_batch(const Plan<T>& p, const PiSrc<T>& s, const PiEpi<T>& e, const T* L
 // number of kernel launches of one iota_batch / pi_batch call
 constexpr int kIotaLaunches = 2, kPiLaunches = 2, kBracketLaunches = 3;
 
-enum PwMode { PW_F = 0, PW_T = 1, PW_GT = 2 };
+enum PwMode : int { PW_F = 0, PW_T = 1, PW_GT = 2 };
 // One bracket evaluation on the padded plan p runs three kernels:
 //   bracket_iota  iota stages A+B of the 24 fields of d (layout per field
 //                 block: value[3], jac[3][3], Lvalue[3], Ljac[3][3], with
@@ -166,7 +177,7 @@ void bracket_iota(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>
                   double* tc_flag = nullptr);
 template <typename T>
 void bracket_cpw(const Plan<T>& p, PwMode mode, const cplx<T>* T2, T* slot, T* slot2, cplx<T>* P2,
-                 cudaStream_t st);
+                 cudaStream_t st, double* tc_flag = nullptr);
 // tc_flag != nullptr selects the tcgen05 form (FP32 plans with p.tc_pi set)
 template <typename T>
 void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T>* P2,

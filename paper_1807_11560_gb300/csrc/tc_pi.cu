@@ -48,6 +48,8 @@ constexpr int kLdA = 8;    // 16-byte loads of the slab per thread, all in fligh
 struct PiTc {
   int KA, KB;        // K of stages A' (2 G3) and B' (2 G2)
   int NA, NB;        // N of stages A' (2 K3) and B' (2 K2)
+  int rows;          // operand rows stored (max(G2, K3), rounded up to 8)
+  int tw;            // floats of the twiddle buffer (hi + lo of the larger stage)
   int tcols;         // TMEM columns allocated
 };
 
@@ -108,14 +110,17 @@ k_pi_ba_tc(Plan<float> p, PiEpi<float> e, const float* __restrict__ Lhat, const 
   const int G2 = G2c ? G2c : p.g.n2, G3 = G3c ? G3c : p.g.n3, K2 = K2c ? K2c : p.b.k2, K3 = K3c ? K3c : p.b.k3;
   const int KA = 2 * G3, KB = 2 * G2, NA = 2 * K3, NB = 2 * K2;
   const int Kmax = KA > KB ? KA : KB;
-  const int R = kMTile * Kmax;
+  // Shared memory: the A operand's stored rows (G2 for A', K3 for B'), hi then
+  // lo, then one twiddle buffer holding E3x for stage A' and then E2x for stage
+  // B'.  An MMA reads 128 rows of A; the rows past the stored ones fall inside
+  // this allocation (checked on the host) and only feed accumulator rows that
+  // are never read.  Keeping the CTA under half the SM's shared memory lets
+  // two CTAs share an SM, so every cluster of a launch is resident at once.
+  const int R = g.rows * Kmax;
   float* Ahi = sm;                                  // A operand (stage A', then stage B')
   float* Alo = sm + R;
-  float* BAhi = sm + 2 * R;                         // E3x
-  float* BAlo = BAhi + NA * KA;
-  float* BBhi = BAlo + NA * KA;                     // E2x
-  float* BBlo = BBhi + NB * KB;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(BBlo + NB * KB);
+  float* Bhi = sm + 2 * R;                          // E3x, then E2x
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Bhi + g.tw);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   float2* Y = reinterpret_cast<float2*>(sm);        // [K2][K3] after stage B' (aliases the operand)
 
@@ -130,12 +135,12 @@ k_pi_ba_tc(Plan<float> p, PiEpi<float> e, const float* __restrict__ Lhat, const 
   // programmatic dependent launch: the next kernel may be scheduled now; the
   // prologue reads constants only, the wait precedes the product field
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  {
-    const int n4 = (2 * NA * KA + 2 * NB * KB) / 4;
-    const float4* src = reinterpret_cast<const float4*>(p.tc_pi);
-    float4* dst = reinterpret_cast<float4*>(BAhi);
-    for (int i = tid; i < n4; i += kThrP) cp_async16p(dst + i, src + i);
-  }
+  auto stage_tw = [&](const float* src, int n) {   // n floats, a multiple of 4
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(Bhi);
+    for (int i = tid; i < n / 4; i += kThrP) cp_async16p(d4 + i, s4 + i);
+  };
+  stage_tw(p.tc_pi, 2 * NA * KA);                   // E3x hi | lo
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(g.tcols)
@@ -221,8 +226,9 @@ k_pi_ba_tc(Plan<float> p, PiEpi<float> e, const float* __restrict__ Lhat, const 
   const int q = warp & 3, cg = warp >> 2;           // lane quadrant, column group (of 2)
   const uint32_t tlane = (uint32_t)(32 * q) << 16;
 
-  if (tid == 0) issue(tbase, Ahi, Alo, BAhi, BAlo, KA, sboA, idA);
+  if (tid == 0) issue(tbase, Ahi, Alo, Bhi, Bhi + NA * KA, KA, sboA, idA);
   if (wait()) {
+    stage_tw(p.tc_pi + 2 * NA * KA, 2 * NB * KB);   // E2x hi | lo, in flight during the re-layout
     // 2. D of A' (lane = x2) -> stage B' operand: row k3, K = (x2, c'), each
     //    lane walking its k3 values in a lane-rotated order
     const int x2 = 32 * q + lane;
@@ -250,10 +256,11 @@ k_pi_ba_tc(Plan<float> p, PiEpi<float> e, const float* __restrict__ Lhat, const 
         }
       }
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (tid == 0) issue(tbase + (uint32_t)NA, Ahi, Alo, BBhi, BBlo, KB, sboB, idB);
+    if (tid == 0) issue(tbase + (uint32_t)NA, Ahi, Alo, Bhi, Bhi + NB * KB, KB, sboB, idB);
     if (wait()) {
       // 3. D of B' (lane = k3) -> Y[k2][k3] (the operand area is free again)
       const int k3 = 32 * q + lane;
@@ -356,11 +363,16 @@ bool pi_tc_geom(const Plan<float>& p, int nper, PiTc& g, size_t& smem) {
   if (g.NA > 256 || g.NB > 256 || g.NA % 16 != 0 || g.NB % 16 != 0) return false;
   if ((G2 / 8) * ((g.KA / 4 + 3) / 4) > kLdA * kWarpsP) return false;   // the slab's loads in registers
   g.tcols = pow2_cols(g.NA + g.NB);
-  if (g.tcols > 512) return false;
-  const size_t opnd = (size_t)2 * kMTile * std::max(g.KA, g.KB) * sizeof(float);
-  if ((size_t)K2 * K3 * sizeof(float2) > opnd) return false;
-  smem = opnd + (size_t)(2 * g.NA * g.KA + 2 * g.NB * g.KB) * sizeof(float) + 16;
-  return smem <= 220 * 1024;
+  if (g.tcols > 256) return false;                  // two CTAs per SM
+  const int Kmax = std::max(g.KA, g.KB);
+  g.rows = (std::max(G2, K3) + 7) / 8 * 8;
+  g.tw = 2 * std::max(g.NA * g.KA, g.NB * g.KB);
+  if ((size_t)K2 * K3 * 2 > (size_t)g.rows * Kmax) return false;   // Y fits the hi rows
+  size_t floats = (size_t)2 * g.rows * Kmax + g.tw;
+  // the 128-row reads of the lo half stay inside the allocation
+  floats = std::max(floats, (size_t)g.rows * Kmax + (size_t)kMTile * Kmax);
+  smem = floats * sizeof(float) + 16;
+  return smem <= 112 * 1024;
 }
 
 template <int G2c, int G3c, int K2c, int K3c>

@@ -1,5 +1,6 @@
-"""The tcgen05 (3xTF32) form of pi stages B'+A' with the bracket epilogue
-(per-evaluation launches on the padded grid) against the FP64 oracle:
+"""The tcgen05 (3xTF32) forms of the bracket evaluation's middle phase (C,
+products, C') and of pi stages B'+A' with the bracket epilogue (per-evaluation
+launches on the padded grid) against the FP64 oracle:
 ad~^dagger and ad~ alone (Eqs. 48-49), the Heun shoot (its epilogues update
 band vectors in place), and the gradient and Gauss-Newton product at shapes
 with one and two 128-row passes of the first stage, ragged K and ragged tiles.
@@ -16,11 +17,12 @@ from helpers import ALPHA, S, SIGMA, host, quantise, rel_V, torch_dev
 
 pytestmark = pytest.mark.gpu
 
-# padded grids (24, 24, 24) / (36, 24, 36) / (48, 48, 48) / (12, 60, 24): one and
-# two 128-row passes of the first stage (nper G2 = 72 .. 180), K2 = 40; the
-# padded grid (12, 12, 9) is outside the tensor-core tiles (the SIMT kernel runs)
+# padded grids (24, 24, 24) / (36, 24, 36) / (48, 48, 48) / (12, 60, 24) /
+# (48, 36, 48) / (12, 12, 9): the tensor-core pi where M2 is a multiple of 8, the
+# tensor-core middle phase where M1 is a multiple of 16 and K1/2 of 4 (48^3 and
+# 48 x 36 x 48), the SIMT kernels elsewhere
 SHAPES = [((32, 32, 32), (16, 16, 16)), ((56, 48, 40), (24, 16, 24)), ((64, 64, 64), (32, 32, 32)),
-          ((20, 44, 30), (8, 40, 16)), ((24, 20, 14), (8, 8, 6))]
+          ((20, 44, 30), (8, 40, 16)), ((24, 20, 14), (8, 8, 6)), ((56, 40, 52), (32, 24, 32))]
 
 
 def _ctx(Ns, Ks, Nt=2):
@@ -52,7 +54,7 @@ def test_tc_pi_shoot_matches_oracle(Ns, Ks):
         assert rel_V(host(out), vs[-1], Ks) < 1e-5
 
 
-@pytest.mark.parametrize("Ns,Ks", [SHAPES[1], SHAPES[3]])
+@pytest.mark.parametrize("Ns,Ks", [SHAPES[1], SHAPES[3], SHAPES[5]])
 def test_tc_pi_gradient_and_hessvec(Ns, Ks):
     import torch
     Nt, seed = 3, 1813
