@@ -684,8 +684,12 @@ inline BAGeom ba_geom(const Plan<T>& p, int ncomp, int nper) {
     --g.KC;
     g.nch = (K2 + g.KC - 1) / g.KC;
   }
-  // slab rows: as many as keep the CTA within 72 KB (three CTAs per SM)
-  const size_t target = 72 * 1024;
+  // slab rows: as many as keep the CTA within 72 KB (three CTAs per SM); on
+  // wide image-grid planes, whose fixed part alone nearly fills that, up to
+  // 150 KB instead: every chunk of rows costs one L2 round trip and two block
+  // barriers, which dominate when only a few rows fit
+  size_t target = 72 * 1024;
+  if (fixed() + (size_t)16 * row > target) target = 150 * 1024;
   const size_t rows = fixed() < target ? (target - fixed()) / row : 0;
   g.XB = std::max(g.KC, (int)std::min<size_t>((size_t)G2, rows));
   return g;

@@ -42,6 +42,10 @@ struct AbTc {
   int KA, KB;   // K of stages A and B (2 K3, 2 K2)
   int NA, NB;   // N of stages A and B (2 G3, 2 G2, rounded up to 16)
   int passes;   // 128-row passes of stage B
+  int rows;     // operand rows stored (max(S K2, S G3 up to 128), rounded up to 8)
+  int tw;       // floats of the twiddle buffer (hi + lo of the larger stage)
+  int tcols;    // TMEM columns allocated
+  int colB;     // first TMEM column of stage B
 };
 
 __device__ __forceinline__ int sfq(int q, int K) { return (2 * q < K) ? q : q - K; }
@@ -93,15 +97,24 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
   g.KB = 2 * K2;
   g.NA = r16d(2 * G3);
   g.NB = r16d(2 * G2);
-  const int R = kMTile * max(g.KA, g.KB);
+  // Shared memory: the A operand's stored rows, hi then lo, then one twiddle
+  // buffer holding E3x for stage A and then E2x for stage B (copied from the
+  // operands expanded once per context).  An MMA reads 128 rows of A; the rows
+  // past the stored ones fall inside this allocation (checked on the host) and
+  // only feed accumulator rows that are never read.  The CTA stays under half
+  // an SM's shared memory (and TMEM), so two work items share an SM.
+  const int R = g.rows * max(g.KA, g.KB);
   float* Ahi = sm;                                  // A operand (stage A, then stage B)
   float* Alo = sm + R;
-  float* BAhi = sm + 2 * R;                         // E3x
-  float* BAlo = BAhi + g.NA * g.KA;
-  float* BBhi = BAlo + g.NA * g.KA;                 // E2x
-  float* BBlo = BBhi + g.NB * g.KB;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(BBlo + g.NB * g.KB);
+  float* Bhi = sm + 2 * R;                          // E3x, then E2x
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Bhi + g.tw);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int nA2 = 2 * g.NA * g.KA, nB2 = 2 * g.NB * g.KB;   // floats of E3x, E2x (hi + lo)
+  auto stage_twx = [&](const float* src, int n) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(Bhi);
+    for (int i = threadIdx.x; i < n / 4; i += kThr) cp_async16(d4 + i, s4 + i);
+  };
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nslab = d.nf * H1;
@@ -110,52 +123,10 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
   // prologue below reads constants only, the wait precedes the band slabs
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
-  // twiddle operands, once per CTA: each complex twiddle fills a 2 x 2 block
-  // of its real form
-  auto stage_tw = [&](const float2* __restrict__ E, int Kc, int G, float* hi, float* lo, int Kx, int N) {
-    for (int base = 0; base < Kc * G; base += 8 * kThr) {
-      float2 e[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int i = base + u * kThr + tid;
-        e[u] = i < Kc * G ? E[i] : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int i = base + u * kThr + tid;
-        if (i < Kc * G) {
-          const int k = i / G, x = i - k * G;
-#pragma unroll
-          for (int c = 0; c < 2; ++c)
-#pragma unroll
-            for (int cp = 0; cp < 2; ++cp) {
-              const float v = twx(e[u], c, cp);
-              const float h = tf32_hi(v);
-              const int o = kmajor_off(2 * x + c, 2 * k + cp, Kx);
-              hi[o] = h;
-              lo[o] = v - h;
-            }
-        }
-      }
-    }
-    for (int i = tid; i < (N - 2 * G) * Kx; i += kThr) {   // zero rows of the N padding
-      const int o = kmajor_off(2 * G + i / Kx, i % Kx, Kx);
-      hi[o] = 0.f;
-      lo[o] = 0.f;
-    }
-  };
-  if (p.tc_ab != nullptr) {                         // expanded once per context: copy
-    const int n4 = (2 * g.NA * g.KA + 2 * g.NB * g.KB) / 4;
-    const float4* src = reinterpret_cast<const float4*>(p.tc_ab);
-    float4* dst = reinterpret_cast<float4*>(BAhi);
-    for (int i = tid; i < n4; i += kThr) cp_async16(dst + i, src + i);
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-  } else {
-    stage_tw(p.E3f, K3, G3, BAhi, BAlo, g.KA, g.NA);
-    stage_tw(p.E2f, K2, G2, BBhi, BBlo, g.KB, g.NB);
-  }
+  stage_twx(p.tc_ab, nA2);                          // E3x hi | lo
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(g.tcols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -170,23 +141,13 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
   asm volatile("griddepcontrol.wait;" ::: "memory");
 
   const uint32_t idA = idesc_tf32(kMTile, g.NA), idB = idesc_tf32(kMTile, g.NB);
-  const uint32_t sboA = (uint32_t)(g.KA >> 2) * 128, sboB = (uint32_t)(g.KB >> 2) * 128;
   uint32_t phase = 0;
   bool ok = true;
   // one 3xTF32 product tile: D (+)= Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T
-  auto issue = [&](uint32_t dcol, const float* ah, const float* al, const float* bh, const float* bl, int K,
-                   uint32_t sbo, uint32_t idesc) {
+  auto issue = [&](uint32_t dcol, uint32_t stride, const float* ah, const float* al, const float* bh,
+                   const float* bl, int K, uint32_t idesc) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    for (int s = 0; s < K / 8; ++s) {
-      const uint32_t so = (uint32_t)s * 256;
-      const uint64_t dah = smem_desc(smem_u32(ah) + so, 128, sbo);
-      const uint64_t dal = smem_desc(smem_u32(al) + so, 128, sbo);
-      const uint64_t dbh = smem_desc(smem_u32(bh) + so, 128, sbo);
-      const uint64_t dbl = smem_desc(smem_u32(bl) + so, 128, sbo);
-      mma_tf32(dcol, dah, dbh, idesc, s > 0 ? 1u : 0u);
-      mma_tf32(dcol, dah, dbl, idesc, 1u);
-      mma_tf32(dcol, dal, dbh, idesc, 1u);
-    }
+    mma_3xtf32<1>(dcol, stride, ah, al, bh, bl, K, idesc);
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(mbar))
                  : "memory");
@@ -212,6 +173,7 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
 
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int sl0 = item * g.S;
+    if (item != (int)blockIdx.x) stage_twx(p.tc_ab, nA2);   // E3x again (E2x held the buffer)
     // 1. stage A operand: the multiplied band slabs, rows (s, k2), K = (k3, c).
     //    A warp takes 8 x 4 tiles (8 rows k2 x 4 columns k3): full 32-byte
     //    sectors from global memory and at most 2-way bank conflicts in the
@@ -268,10 +230,14 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
         }
       }
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");       // E3x has landed
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (tid == 0) issue(tbase, Ahi, Alo, BAhi, BAlo, g.KA, sboA, idA);
+    // stage A in columns [0, 2 NA); stage B in the same columns when one pass
+    // reads stage A's result once, else after them (every pass re-reads it)
+    if (tid == 0) issue(tbase, (uint32_t)g.NA, Ahi, Alo, Bhi, Bhi + g.NA * g.KA, g.KA, idA);
     if (!wait()) break;
+    stage_twx(p.tc_ab + nA2, nB2);                 // E2x hi | lo, in flight during the re-layout
     // 2. D_A -> stage B operand, 128 rows (s, x3) per pass
     const int r = 32 * q + lane;                     // D_A row (s, k2)
     const int js = r / K2, k2 = r - js * K2;
@@ -279,7 +245,7 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
       if (ps > 0 && !wait()) break;                  // the previous pass has read the operand
       for (int c0 = 16 * cg; c0 < g.NA; c0 += 64) {
         float v[16];
-        tmem_ld16(tbase + tlane + (uint32_t)c0, v);
+        tmem_ld16_sum<1>(tbase + tlane + (uint32_t)c0, (uint32_t)g.NA, v);
         if (js < g.S) {
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -302,10 +268,12 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
           }
         }
       }
+      asm volatile("cp.async.wait_all;\n" ::: "memory");     // E2x has landed
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
-      if (tid == 0) issue(tbase + (uint32_t)(g.NA + ps * g.NB), Ahi, Alo, BBhi, BBlo, g.KB, sboB, idB);
+      if (tid == 0)
+        issue(tbase + (uint32_t)(g.colB + ps * g.NB), (uint32_t)g.NB, Ahi, Alo, Bhi, Bhi + g.NB * g.KB, g.KB, idB);
     }
     if (!ok || !wait()) break;
     // 3. D_B -> T2[f][h][x2][x3]
@@ -317,7 +285,7 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
       float2* __restrict__ dst = T2 + (long long)(live ? sl : 0) * G2 * G3 + x3;
       for (int c0 = 16 * cg; c0 < g.NB; c0 += 64) {
         float v[16];
-        tmem_ld16(tbase + tlane + (uint32_t)(g.NA + ps * g.NB + c0), v);
+        tmem_ld16_sum<1>(tbase + tlane + (uint32_t)(g.colB + ps * g.NB + c0), (uint32_t)g.NB, v);
         if (live) {
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -334,10 +302,16 @@ k_iota_ab_tc(Plan<float> p, IotaDesc<float> d, const float* __restrict__ Lhat, f
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(g.tcols) : "memory");
 }
 
 int r16(int n) { return ((n + 15) / 16) * 16; }
+
+int pow2t(int n) {
+  int c = 32;
+  while (c < n) c *= 2;
+  return c;
+}
 
 bool ab_tc_geom(const Plan<float>& p, AbTc& g, size_t& smem) {
   const int K2 = p.b.k2, K3 = p.b.k3, G2 = p.g.n2, G3 = p.g.n3;
@@ -347,13 +321,23 @@ bool ab_tc_geom(const Plan<float>& p, AbTc& g, size_t& smem) {
   g.NA = r16(2 * G3);
   g.NB = r16(2 * G2);
   if (g.NA > 256 || g.NB > 256) return false;
-  for (g.S = kMTile / K2; g.S >= 1; --g.S) {
-    g.passes = (g.S * G3 + kMTile - 1) / kMTile;
-    if (g.NA + g.passes * g.NB <= 512) break;
-  }
-  if (g.S < 1) return false;
-  smem = (size_t)(2 * kMTile * std::max(g.KA, g.KB) + 2 * g.NA * g.KA + 2 * g.NB * g.KB) * sizeof(float) + 16;
-  return smem <= 200 * 1024;
+  // about 64 rows of band slabs per item: enough items for every SM, and a
+  // short chain per item
+  g.S = std::max(1, std::min(kMTile / K2, 64 / K2));
+  g.passes = (g.S * G3 + kMTile - 1) / kMTile;
+  // stage B reuses stage A's columns when a single pass reads stage A's
+  // result once
+  g.colB = g.passes == 1 ? 0 : g.NA;
+  g.tcols = pow2t(std::max(g.NA, g.colB + g.passes * g.NB));
+  if (g.tcols > 256) return false;                  // two items per SM
+  const int Kmax = std::max(g.KA, g.KB);
+  g.rows = (std::max(g.S * K2, std::min(g.S * G3, kMTile)) + 7) / 8 * 8;
+  g.tw = 2 * std::max(g.NA * g.KA, g.NB * g.KB);
+  size_t floats = (size_t)2 * g.rows * Kmax + g.tw;
+  // the 128-row reads of the lo half stay inside the allocation
+  floats = std::max(floats, (size_t)g.rows * Kmax + (size_t)kMTile * Kmax);
+  smem = floats * sizeof(float) + 16;
+  return smem <= 112 * 1024;
 }
 
 }  // namespace
@@ -390,7 +374,7 @@ cudaError_t launch_ab_tc(const Plan<float>& p, const IotaDesc<float>& d, const f
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const int nitems = (d.nf * p.b.h1 + g.S - 1) / g.S;
-  const unsigned grid = (unsigned)std::min(nitems, sms);
+  const unsigned grid = (unsigned)std::min(nitems, 2 * sms);
   // programmatic stream serialisation: the prologue (twiddle copy, TMEM
   // allocation) overlaps the tail of the previous kernel
   cudaLaunchConfig_t cfg = {};
@@ -412,9 +396,7 @@ cudaError_t iota_ab_tc(const Plan<float>& p, const IotaDesc<float>& d, const flo
   AbTc g;
   size_t smem = 0;
   if (!ab_tc_geom(p, g, smem)) return cudaErrorInvalidValue;
-  // at least 140 KB: one CTA (and one 512-column TMEM allocation) per SM, and
-  // no room beside it for the image-grid kernel's TMEM either
-  smem = std::max<size_t>(smem, 140 * 1024);
+  if (p.tc_ab == nullptr) return cudaErrorInvalidValue;
   const int K2 = p.b.k2, K3 = p.b.k3, G2 = p.g.n2, G3 = p.g.n3;
   if (K2 == 32 && K3 == 32 && G2 == 48 && G3 == 48)
     return launch_ab_tc<32, 32, 48, 48>(p, d, Lhat, T2, g, smem, flag, st);

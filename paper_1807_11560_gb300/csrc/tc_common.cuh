@@ -71,5 +71,63 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// the same 32-lane x 16-column load, the wait left to the caller (several
+// loads in flight, then tmem_wait)
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 16 columns summed over NACC accumulators `stride` columns apart (the 3xTF32
+// products may be kept in separate accumulators; NACC = 1: one accumulator)
+template <int NACC>
+__device__ __forceinline__ void tmem_ld16_sum(uint32_t taddr, uint32_t stride, float* v) {
+  uint32_t r[NACC][16];
+#pragma unroll
+  for (int a = 0; a < NACC; ++a) tmem_ld16_async(taddr + (uint32_t)a * stride, r[a]);
+  tmem_wait();
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    float x = __uint_as_float(r[0][j]);
+#pragma unroll
+    for (int a = 1; a < NACC; ++a) x += __uint_as_float(r[a][j]);
+    v[j] = x;
+  }
+}
+
+// K-loop of one 3xTF32 product tile over NACC accumulators `stride` columns
+// apart: hi*hi into accumulator 0, hi*lo and lo*hi into 1 and 2 (NACC = 3) or
+// both into 1 (NACC = 2).  Descriptors: K-major, no swizzle, 16-byte rows,
+// LBO = 128 bytes, SBO = (K / 4) * 128 bytes; K a multiple of 8.
+template <int NACC>
+__device__ __forceinline__ void mma_3xtf32(uint32_t dcol, uint32_t stride, const float* ah, const float* al,
+                                           const float* bh, const float* bl, int K, uint32_t idesc) {
+  const uint32_t sbo = (uint32_t)(K >> 2) * 128;
+  for (int s = 0; s < K / 8; ++s) {
+    const uint32_t so = (uint32_t)s * 256;
+    const uint64_t dah = smem_desc(smem_u32(ah) + so, 128, sbo);
+    const uint64_t dal = smem_desc(smem_u32(al) + so, 128, sbo);
+    const uint64_t dbh = smem_desc(smem_u32(bh) + so, 128, sbo);
+    const uint64_t dbl = smem_desc(smem_u32(bl) + so, 128, sbo);
+    const uint32_t first = s > 0 ? 1u : 0u;
+    mma_tf32(dcol, dah, dbh, idesc, first);
+    if (NACC == 3) {
+      mma_tf32(dcol + stride, dah, dbl, idesc, first);
+      mma_tf32(dcol + 2 * stride, dal, dbh, idesc, first);
+    } else if (NACC == 2) {
+      mma_tf32(dcol + stride, dah, dbl, idesc, first);
+      mma_tf32(dcol + stride, dal, dbh, idesc, 1u);
+    } else {
+      mma_tf32(dcol, dah, dbl, idesc, 1u);
+      mma_tf32(dcol, dal, dbh, idesc, 1u);
+    }
+  }
+}
+
 }  // namespace tc
 }  // namespace lddmm

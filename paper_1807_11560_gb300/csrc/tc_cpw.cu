@@ -182,19 +182,9 @@ k_cpw_tc(Plan<float> p, const float2* __restrict__ T2, float* __restrict__ slot,
   uint32_t phase = 0;
   bool ok = true;
   // one 3xTF32 product tile: D (+)= Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T
-  auto issue = [&](uint32_t dcol, const float* ah, const float* al, const float* bh, const float* bl, int K,
-                   uint32_t idesc) {
-    const uint32_t sbo = (uint32_t)(K >> 2) * 128;
-    for (int s = 0; s < K / 8; ++s) {
-      const uint32_t so = (uint32_t)s * 256;
-      const uint64_t dah = smem_desc(smem_u32(ah) + so, 128, sbo);
-      const uint64_t dal = smem_desc(smem_u32(al) + so, 128, sbo);
-      const uint64_t dbh = smem_desc(smem_u32(bh) + so, 128, sbo);
-      const uint64_t dbl = smem_desc(smem_u32(bl) + so, 128, sbo);
-      mma_tf32(dcol, dah, dbh, idesc, s > 0 ? 1u : 0u);
-      mma_tf32(dcol, dah, dbl, idesc, 1u);
-      mma_tf32(dcol, dal, dbh, idesc, 1u);
-    }
+  auto issue = [&](uint32_t dcol, uint32_t stride, const float* ah, const float* al, const float* bh,
+                   const float* bl, int K, uint32_t idesc) {
+    mma_3xtf32<1>(dcol, stride, ah, al, bh, bl, K, idesc);
   };
   auto commit = [&]() {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -224,7 +214,8 @@ k_cpw_tc(Plan<float> p, const float2* __restrict__ T2, float* __restrict__ slot,
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t id1 = idesc_tf32(kMTile, g.N1);
     for (int t = 0; t < g.tiles1; ++t)
-      issue(tbase + (uint32_t)(t * g.N1), A1hi + t * rowsA1, A1lo + t * rowsA1, B1, B1 + g.N1 * g.K1, g.K1, id1);
+      issue(tbase + (uint32_t)(t * g.N1), (uint32_t)(g.tiles1 * g.N1), A1hi + t * rowsA1, A1lo + t * rowsA1, B1,
+            B1 + g.N1 * g.K1, g.K1, id1);
     commit();
   }
   if (wait()) {
@@ -235,7 +226,7 @@ k_cpw_tc(Plan<float> p, const float2* __restrict__ T2, float* __restrict__ slot,
       const int row = t * kMTile + 32 * q;
       if (row >= g.rows1) continue;                 // the whole warp skips: uniform
       float v[16];
-      tmem_ld16(tbase + tlane + (uint32_t)(t * g.N1 + c0), v);
+      tmem_ld16_sum<1>(tbase + tlane + (uint32_t)(t * g.N1 + c0), (uint32_t)(g.tiles1 * g.N1), v);
       const int r = row + lane;
       if (r < g.rows1) {
         const int f = r / TP, pp = r - f * TP;
@@ -301,7 +292,8 @@ k_cpw_tc(Plan<float> p, const float2* __restrict__ T2, float* __restrict__ slot,
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      issue(tbase + (uint32_t)(g.tiles1 * g.N1), A2hi, A2lo, B2, B2 + g.N2 * g.K2, g.K2, idesc_tf32(kMTile, g.N2));
+      // C' reuses the columns of C (read out above)
+      issue(tbase, (uint32_t)g.N2, A2hi, A2lo, B2, B2 + g.N2 * g.K2, g.K2, idesc_tf32(kMTile, g.N2));
       commit();
     }
     if (wait()) {
@@ -310,7 +302,7 @@ k_cpw_tc(Plan<float> p, const float2* __restrict__ T2, float* __restrict__ slot,
       if (32 * q < NP * TP) {
         for (int c0 = 16 * cg; c0 < g.N2; c0 += 32) {
           float v[16];
-          tmem_ld16(tbase + tlane + (uint32_t)(g.tiles1 * g.N1 + c0), v);
+          tmem_ld16_sum<1>(tbase + tlane + (uint32_t)c0, (uint32_t)g.N2, v);
           if (r < NP * TP) {
             const int qf = r / TP, pp = r - qf * TP;
             float2* dst = P2 + (long long)qf * H1 * P + p0 + pp;
@@ -353,7 +345,7 @@ bool cpw_tc_geom(const Plan<float>& p, int NP, CpwTc& g, size_t& smem) {
   g.rows2s = (NP * kTPc + 7) / 8 * 8;
   if (NP * kTPc > kMTile) return false;
   g.SF = G1 * kTPc + ((G1 * kTPc) % 32 == 0 ? 8 : 0);
-  g.tcols = pow2c(g.tiles1 * g.N1 + g.N2);
+  g.tcols = pow2c(std::max(g.tiles1 * g.N1, g.N2));   // C' reuses C's columns
   if (g.tcols > 256) return false;                  // two tiles per SM
   // layout (floats): A2 hi, A2 lo, A1 hi, A1 lo, E1fx hi|lo, E1bx hi|lo, barrier
   const int a2 = g.rows2s * g.K2;

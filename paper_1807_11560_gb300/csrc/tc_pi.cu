@@ -188,22 +188,13 @@ k_pi_ba_tc(Plan<float> p, PiEpi<float> e, const float* __restrict__ Lhat, const 
   const uint32_t tbase = *tslot;
 
   const uint32_t idA = idesc_tf32(kMTile, NA), idB = idesc_tf32(kMTile, NB);
-  const uint32_t sboA = (uint32_t)(KA >> 2) * 128, sboB = (uint32_t)(KB >> 2) * 128;
   uint32_t phase = 0;
   bool ok = true;
-  auto issue = [&](uint32_t dcol, const float* ah, const float* al, const float* bh, const float* bl, int K,
-                   uint32_t sbo, uint32_t idesc) {
+  // both stages accumulate in columns 0 .. N (stage B' after A' has been read)
+  auto issue = [&](const float* ah, const float* al, const float* bh, const float* bl, int K, uint32_t stride,
+                   uint32_t idesc) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    for (int s = 0; s < K / 8; ++s) {
-      const uint32_t so = (uint32_t)s * 256;
-      const uint64_t dah = smem_desc(smem_u32(ah) + so, 128, sbo);
-      const uint64_t dal = smem_desc(smem_u32(al) + so, 128, sbo);
-      const uint64_t dbh = smem_desc(smem_u32(bh) + so, 128, sbo);
-      const uint64_t dbl = smem_desc(smem_u32(bl) + so, 128, sbo);
-      mma_tf32(dcol, dah, dbh, idesc, s > 0 ? 1u : 0u);
-      mma_tf32(dcol, dah, dbl, idesc, 1u);
-      mma_tf32(dcol, dal, dbh, idesc, 1u);
-    }
+    mma_3xtf32<1>(tbase, stride, ah, al, bh, bl, K, idesc);
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(mbar))
                  : "memory");
@@ -226,7 +217,7 @@ k_pi_ba_tc(Plan<float> p, PiEpi<float> e, const float* __restrict__ Lhat, const 
   const int q = warp & 3, cg = warp >> 2;           // lane quadrant, column group (of 2)
   const uint32_t tlane = (uint32_t)(32 * q) << 16;
 
-  if (tid == 0) issue(tbase, Ahi, Alo, Bhi, Bhi + NA * KA, KA, sboA, idA);
+  if (tid == 0) issue(Ahi, Alo, Bhi, Bhi + NA * KA, KA, (uint32_t)NA, idA);
   if (wait()) {
     stage_tw(p.tc_pi + 2 * NA * KA, 2 * NB * KB);   // E2x hi | lo, in flight during the re-layout
     // 2. D of A' (lane = x2) -> stage B' operand: row k3, K = (x2, c'), each
@@ -235,7 +226,7 @@ k_pi_ba_tc(Plan<float> p, PiEpi<float> e, const float* __restrict__ Lhat, const 
     if (32 * q < G2) {
       for (int c0 = 16 * cg; c0 < NA; c0 += 32) {
         float v[16];
-        tmem_ld16(tbase + tlane + (uint32_t)c0, v);
+        tmem_ld16_sum<1>(tbase + tlane + (uint32_t)c0, (uint32_t)NA, v);
         if (x2 < G2) {
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -260,14 +251,14 @@ k_pi_ba_tc(Plan<float> p, PiEpi<float> e, const float* __restrict__ Lhat, const 
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (tid == 0) issue(tbase + (uint32_t)NA, Ahi, Alo, Bhi, Bhi + NB * KB, KB, sboB, idB);
+    if (tid == 0) issue(Ahi, Alo, Bhi, Bhi + NB * KB, KB, (uint32_t)NB, idB);
     if (wait()) {
       // 3. D of B' (lane = k3) -> Y[k2][k3] (the operand area is free again)
       const int k3 = 32 * q + lane;
       if (32 * q < K3) {
         for (int c0 = 16 * cg; c0 < NB; c0 += 32) {
           float v[16];
-          tmem_ld16(tbase + tlane + (uint32_t)(NA + c0), v);
+          tmem_ld16_sum<1>(tbase + tlane + (uint32_t)c0, (uint32_t)NB, v);
           if (k3 < K3) {
 #pragma unroll
             for (int i = 0; i < 8; ++i)
@@ -362,7 +353,7 @@ bool pi_tc_geom(const Plan<float>& p, int nper, PiTc& g, size_t& smem) {
   g.NB = 2 * K2;
   if (g.NA > 256 || g.NB > 256 || g.NA % 16 != 0 || g.NB % 16 != 0) return false;
   if ((G2 / 8) * ((g.KA / 4 + 3) / 4) > kLdA * kWarpsP) return false;   // the slab's loads in registers
-  g.tcols = pow2_cols(g.NA + g.NB);
+  g.tcols = pow2_cols(std::max(g.NA, g.NB));       // stage B' reuses the columns of stage A'
   if (g.tcols > 256) return false;                  // two CTAs per SM
   const int Kmax = std::max(g.KA, g.KB);
   g.rows = (std::max(G2, K3) + 7) / 8 * 8;
