@@ -56,6 +56,9 @@ def parse():
                     help="image-grid band-to-grid transforms on tcgen05 (3xTF32): auto = grids >= 2^20 voxels")
     ap.add_argument("--persistent", default="auto", choices=["auto", "on", "off"],
                     help="band-limited sweeps as one persistent kernel: auto = padded grids up to 32^3")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "3xtf32", "bf16x3"],
+                    help="fp32: tensor cores per --tensor-cores (3xTF32); 3xtf32 / bf16x3: every contraction "
+                         "with a tensor-core kernel for its sizes on tcgen05 with that operand split")
     ap.add_argument("--grid", default=None,
                     help="override the workload's image grid, e.g. 64,64,64 (a smaller case of the same "
                          "phantom and band, for kernel captures)")
@@ -326,7 +329,7 @@ def run_gpu(args):
     I0, I1 = inputs.make_pair(kind, Ns, rank_seed(seed, rank))
     I0d = torch.as_tensor(I0, dtype=torch.float32, device=dev)
     I1d = torch.as_tensor(I1, dtype=torch.float32, device=dev)
-    ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision="fp32",
+    ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision=args.precision,
                   tensor_cores={"auto": "auto", "on": True, "off": False}[args.tensor_cores], state=args.state,
                   persistent={"auto": "auto", "on": True, "off": False}[args.persistent])
     ctx.set_images(I0d, I1d)
@@ -483,8 +486,9 @@ def run_gpu(args):
                                f"{N_PCG} PCG Hessvecs, Armijo)",
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{world}",
-                       "tensor_cores": f"{args.tensor_cores} (tcgen05 3xTF32 image-grid iota; "
-                                       "auto = grids of at least 2^20 voxels)",
+                       "precision": args.precision,
+                       "tensor_cores": f"{args.tensor_cores} (tcgen05 3xTF32: image-grid iota on grids of at "
+                                       "least 2^20 voxels, bracket evaluations launched per evaluation)",
                        "tiles": dict(zip(("iota_ab_twiddles", "cpw_pencils", "pi_rows"), ctx.tiles))},
             "gn_solve_s": 1e-3 * statistics.mean(step_ms),
             "gn_solve_note": f"mean timed step: one lddmm_gn_solve call ({rep_t['gn_iters']} GN iterations and "

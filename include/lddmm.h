@@ -74,7 +74,18 @@ typedef enum {
                             failure in lddmm_report.ls_failed instead */
 } lddmm_status;
 
-typedef enum { LDDMM_FP64 = 0, LDDMM_FP32 = 1 } lddmm_precision;
+/* Arithmetic of a context.  LDDMM_FP64: double throughout.  LDDMM_FP32:
+ * float data and arithmetic with FP64 reductions; the tensor cores take the
+ * contractions as opts.tensor_cores says (3xTF32 split).  The two split modes
+ * are FP32 contexts (float / complex64 arrays) whose contractions run on the
+ * tcgen05 tensor cores wherever a kernel covers their sizes (opts.tensor_cores
+ * is then 2): LDDMM_3XTF32 splits every operand x = hi + lo into two TF32
+ * values and sums three TF32 products; LDDMM_BF16X3 splits the operands of the
+ * image-grid band-to-grid stage into three BF16 values (hi + mid + lo) and sums
+ * six BF16 products (the other tensor-core kernels keep 3xTF32).  Every mode
+ * agrees with FP64 to FP32 rounding (~1e-7 relative per transform).  FP32 with
+ * opts.tensor_cores = 0 is the plain FP32 SIMT form. */
+typedef enum { LDDMM_FP64 = 0, LDDMM_FP32 = 1, LDDMM_3XTF32 = 2, LDDMM_BF16X3 = 3 } lddmm_precision;
 
 typedef struct {
   int precision;        /* lddmm_precision; default LDDMM_FP32 */

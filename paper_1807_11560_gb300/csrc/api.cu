@@ -78,6 +78,7 @@ struct Impl {
   double alpha = 0, sigma = 1, dt = 1;
   long long Nvol = 0, Mvol = 0, Kvol = 0;
   lddmm_opts opts{};
+  int split = 0;             // FP32 tensor-core split of the image-grid transform: 0 3xTF32, 1 BF16x3
   cudaStream_t st = nullptr;
   Plan<T> full{}, pad{};
   T* Lhat = nullptr;
@@ -377,6 +378,7 @@ struct Impl {
 
     make_plan(full, N);
     make_plan(pad, M);
+    full.split = split;
     if (max_smem_needed<T>(full, 1, false) > smem_limit() || max_smem_needed<T>(pad, 3, true) > smem_limit()) {
       *err = "grid or band too large for the transform tiles (N_3 <= 1024, shared memory)";
       throw Fail{LDDMM_EINVAL};
@@ -1789,7 +1791,15 @@ int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, doubl
   lddmm_opts o;
   lddmm_default_opts(&o);
   if (opts) o = *opts;
-  if (o.precision != LDDMM_FP32 && o.precision != LDDMM_FP64) return LDDMM_EINVAL;
+  if (o.precision < LDDMM_FP64 || o.precision > LDDMM_BF16X3) return LDDMM_EINVAL;
+  // the split modes are FP32 contexts whose contractions take the tensor cores
+  // wherever a tcgen05 kernel covers their sizes
+  int split = 0;
+  if (o.precision == LDDMM_3XTF32 || o.precision == LDDMM_BF16X3) {
+    split = o.precision == LDDMM_BF16X3 ? 1 : 0;
+    o.precision = LDDMM_FP32;
+    o.tensor_cores = 2;
+  }
   if (o.state_eq != 0 && o.state_eq != 1) return LDDMM_EINVAL;
   if (o.state_eq == 1 && o.newton != 0) return LDDMM_EINVAL;
   if (o.debug_stall < 0) return LDDMM_EINVAL;
@@ -1814,6 +1824,7 @@ int lddmm_create(lddmm_ctx** out, int ndim, const int* grid, const int* K, doubl
     auto* im = new (std::nothrow) Impl<float>();
     if (!im) { delete ctx; return LDDMM_ENOMEM; }
     im->err = &ctx->err;
+    im->split = split;
     ctx->impl = im;
     rc = lddmm::guarded(ctx, [&] { im->create(ndim, grid, K, alpha, s, sigma, Nt, o); });
   }

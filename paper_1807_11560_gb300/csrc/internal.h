@@ -61,6 +61,8 @@ struct Plan {
   // memory (iota A+B); tp = pencils per tile (C/products/C'); kc = band rows
   // per item (pi B'/A')
   int tws = 0, tp = 0, kc = 0;
+  // split of the FP32 tensor-core image-grid transform: 0 3xTF32, 1 BF16x3
+  int split = 0;
   // FP32 padded plans: the tcgen05 iota A+B twiddle operands, expanded once
   // into the kernel's shared-memory layout (nullptr: expanded in the kernel)
   const float* tc_ab = nullptr;

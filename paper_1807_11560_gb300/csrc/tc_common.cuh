@@ -47,6 +47,26 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
       : "memory");
 }
 
+// instruction descriptor: kind::f16 with A = B = BF16 (the two operands of one
+// MMA must have the same type), D = F32, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// element offset of (row r, k) in a K-major no-swizzle operand tile of 16-bit
+// elements with Kp columns: core matrix (r/8, k/8) of 8 rows x 8 elements
+__device__ __forceinline__ int kmajor_off16(int r, int k, int Kp) {
+  return (((r >> 3) * (Kp >> 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
   uint32_t ok;
   asm volatile(

@@ -16,7 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblddmm.so")
 _lib = None
 
-LDDMM_FP64, LDDMM_FP32 = 0, 1
+LDDMM_FP64, LDDMM_FP32, LDDMM_3XTF32, LDDMM_BF16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": LDDMM_FP64, "fp32": LDDMM_FP32, "3xtf32": LDDMM_3XTF32, "bf16x3": LDDMM_BF16X3}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENONFINITE",
           6: "ETIMEOUT", 7: "ENOTCONV"}
 
@@ -188,6 +189,9 @@ class Context:
     (Id - alpha Lap)^s; sigma: data weight 1/sigma^2; Nt: time steps.
     state: "image" (the image state equation, Section 3.2) or "deformation"
     (the band-limited deformation state equation, Section 3.3).
+    precision: "fp64", "fp32" (tensor cores as ``tensor_cores`` says),
+    "3xtf32" or "bf16x3" (FP32 arrays; contractions on the tensor cores with
+    that operand split wherever a kernel covers their sizes).
     """
 
     def __init__(self, grid, K, alpha, s, sigma, Nt, precision="fp32", stream=None,
@@ -202,7 +206,9 @@ class Context:
         self.complex = "complex128" if precision == "fp64" else "complex64"
         o = Opts()
         L.lddmm_default_opts(ctypes.byref(o))
-        o.precision = LDDMM_FP64 if precision == "fp64" else LDDMM_FP32
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision is one of {sorted(PRECISIONS)}")
+        o.precision = PRECISIONS[precision]
         o.stream = stream
         o.use_graphs = 1 if use_graphs else 0
         o.persistent = {True: 2, False: 0, "auto": 1}[persistent]

@@ -72,3 +72,47 @@ def test_tensor_core_bracket_iota_ab(Ns, Ks):
     assert abs(E - lin.E) / lin.E < 1e-6
     assert rel_V(g, lin.g, Ks) < 1e-5
     assert rel_V(Hp, P.hessvec(lin, p), Ks) < 1e-5
+
+
+# the two operand splits of the tensor-core transforms against the FP64 oracle
+# and against each other: the image-grid band-to-grid stage (2^21 voxels, and a
+# ragged 100 x 36 x 20 grid) and the whole gradient / Gauss-Newton product
+@pytest.mark.parametrize("Ns,Ks", [((128, 128, 128), (16, 16, 16)), ((100, 36, 20), (10, 8, 6)),
+                                   ((160, 192, 160), (32, 32, 32))])
+def test_bf16x3_and_3xtf32_iota_match_oracle(Ns, Ks):
+    import torch
+    d = len(Ns)
+    a = quantise(inputs.random_bl(Ks, d, 3, 2.0, Ns), "fp32")
+    ref = bl.iota(a, Ns)
+    errs = {}
+    for prec in ("3xtf32", "bf16x3", "fp32"):
+        with Context(Ns, Ks, ALPHA, S, SIGMA, 2, precision=prec,
+                     tensor_cores=False if prec == "fp32" else "auto") as ctx:
+            out = torch.empty((d,) + Ns, device="cuda", dtype=torch.float32)
+            ctx.iota(torch_dev(a, "fp32"), d, out)
+            errs[prec] = rel_2(host(out), ref)
+    print(f"{Ns} iota rel. err: " + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    assert errs["3xtf32"] < 4e-6 and errs["bf16x3"] < 4e-6
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3"])
+def test_split_modes_gradient_and_hessvec(prec):
+    kind, Ns, Ks, seed, Nt = "ellipsoids", (64, 56, 48), (16, 16, 16), 43, 3
+    import torch
+    I0, I1 = inputs.make_pair(kind, Ns, seed, max_disp=2.0)
+    I0, I1 = quantise(I0, "fp32"), quantise(I1, "fp32")
+    v0 = quantise(inputs.random_bl(Ks, 3, seed + 1, 2.0, Ns), "fp32")
+    p = quantise(inputs.random_bl(Ks, 3, seed + 2, 1.0, Ns), "fp32")
+    from oracle import objective
+    P = objective.Problem(I0, I1, Ks, ALPHA, S, SIGMA, Nt)
+    lin = P.gradient(v0)
+    with Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision=prec) as ctx:
+        ctx.set_images(torch_dev(I0, "fp32"), torch_dev(I1, "fp32"))
+        g = torch.empty((3,) + Ks, device="cuda", dtype=torch.complex64)
+        E = ctx.gradient(torch_dev(v0, "fp32"), g)
+        Hp = torch.empty_like(g)
+        ctx.hessvec(torch_dev(p, "fp32"), Hp)
+        g, Hp = host(g), host(Hp)
+    assert abs(E - lin.E) / lin.E < 1e-6
+    assert rel_V(g, lin.g, Ks) < 1e-5
+    assert rel_V(Hp, P.hessvec(lin, p), Ks) < 1e-5
