@@ -557,7 +557,9 @@ def run_population(args):
 
     made = make("auto")
     timed(made, args.warmup, 0)
+    clocks = Clocks()
     value, step_s, v_tc = timed(made, args.steps, 0)
+    clk = clocks.stop()
     seq_value, _, _ = timed(made, 1, 1)
     held = sum(m[0].device_bytes for m in made)
     for m in made:
@@ -583,6 +585,7 @@ def run_population(args):
         "plain_fp32_value": plain_value,
         "split_vs_plain_rel_update_diff_max": max(diffs),
         "device_bytes_held": held,
+        "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 

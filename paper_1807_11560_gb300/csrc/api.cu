@@ -1382,9 +1382,14 @@ struct Impl {
       cuda(cudaEventRecord(ev, st), "event record");
       cuda(cudaStreamWaitEvent(cap, ev, 0), "wait");
       cuda(cudaGraphLaunch(exec, cap), "graph launch");
-      graph_pending = !graph_pairs.empty();
       cuda(cudaEventRecord(ev, cap), "event record");
       cuda(cudaStreamWaitEvent(st, ev, 0), "wait");
+      if (!graph_pairs.empty()) {
+        // probing inside the graph: the next replay re-records the same
+        // events, so read this replay's pairs now
+        graph_pending = true;
+        sync("probe graph replay");
+      }
       launches += newton ? hv_nodes_newton : hv_nodes;
     } else {
       enqueue_hessvec(newton);

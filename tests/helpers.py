@@ -97,3 +97,18 @@ def fd_data_term(task):
 def spawn_pool(n):
     import multiprocessing as mp
     return mp.get_context("spawn").Pool(n)
+
+
+def oracle_grad_hessvec(task):
+    """(E, g, H p) of the FP64 oracle for one workload entry (kind, grid, band,
+    Nt, seed) with the seeded v0 and p of the batch tests (runs in a worker)."""
+    from oracle import objective
+    from paper_1807_11560_gb300 import inputs
+    kind, Ns, Ks, Nt, seed = task
+    I0, I1 = inputs.make_pair(kind, Ns, seed)
+    I0, I1 = quantise(I0, "fp32"), quantise(I1, "fp32")
+    v0 = quantise(inputs.random_bl(Ks, 3, seed + 1, 2.0, Ns), "fp32")
+    p = quantise(inputs.random_bl(Ks, 3, seed + 2, 1.0, Ns), "fp32")
+    P = objective.Problem(I0, I1, Ks, ALPHA, S, SIGMA, Nt)
+    lin = P.gradient(v0)
+    return lin.E, lin.g, P.hessvec(lin, p)
