@@ -98,13 +98,14 @@ typedef struct {
                            (grid barriers with bounded waits): 0 never (three kernels per
                            bracket evaluation), 1 when the padded product grid has at
                            most 32^3 points (default), 2 always */
-  int tensor_cores;     /* FP32 contexts, tcgen05 tensor cores with the 3xTF32 split for
-                           the band-to-grid transforms: iota stage C on the image grid
-                           and iota stages A+B of the bracket evaluations launched per
-                           evaluation (padded grids above 32^3 points, K2 a multiple of
-                           8, K3 of 4, tiles that fit).  0 never; 1 (default) for image
-                           grids of at least 2^20 voxels and those padded grids; 2
-                           whenever supported */
+  int tensor_cores;     /* FP32 contexts, tcgen05 tensor cores with the 3xTF32 split:
+                           iota stage C on the image grid, and the three kernels of a
+                           bracket evaluation launched per evaluation (iota A+B;
+                           C, the bracket products and C'; pi B'+A' with the
+                           epilogue), each where its tile geometry fits the sizes
+                           (the SIMT kernel otherwise).  0 never; 1 (default) for
+                           image grids of at least 2^20 voxels and padded grids
+                           above 32^3 points; 2 whenever supported */
   int recompute;        /* image-grid histories of the time sweeps (velocity grids v_n,
                            characteristic displacements, states m_n, incremental
                            velocity grids): 0 keep all Nt + 1 steps (default); 1 keep

@@ -57,11 +57,9 @@ void launch_pdl(void (*kern)(KArgs...), unsigned grid, size_t smem, cudaStream_t
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute at[2];
   cfg.attrs = at;
-  cfg.numAttrs = kUsePdl ? 1 : 0;
+  cfg.numAttrs = chain_attrs(at);
   cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 

@@ -20,6 +20,16 @@ constexpr bool kUsePdl = false;
 constexpr bool kUsePdl = true;
 #endif
 
+// Launch attributes of the bracket-evaluation chain, written from at[0]:
+// programmatic stream serialisation, unless built with LDDMM_NO_PDL.
+// Returns the number of attributes written (at most 1).
+inline unsigned chain_attrs(cudaLaunchAttribute* at) {
+  if (!kUsePdl) return 0;
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  return 1;
+}
+
 template <typename T> struct CplxOf;
 template <> struct CplxOf<float> { using type = float2; };
 template <> struct CplxOf<double> { using type = double2; };

@@ -382,11 +382,9 @@ cudaError_t launch_ab_tc(const Plan<float>& p, const IotaDesc<float>& d, const f
   cfg.blockDim = dim3(kThr);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute at[2];
   cfg.attrs = at;
-  cfg.numAttrs = kUsePdl ? 1 : 0;
+  cfg.numAttrs = chain_attrs(at);
   if ((e = cudaLaunchKernelEx(&cfg, kern, p, d, Lhat, T2, g, flag)) != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -406,11 +406,9 @@ cudaError_t cpw_tc(const Plan<float>& p, PwMode mode, const float2* T2, float* s
   cfg.blockDim = dim3(kThrC);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute at[2];
   cfg.attrs = at;
-  cfg.numAttrs = kUsePdl ? 1 : 0;
+  cfg.numAttrs = chain_attrs(at);
   cudaError_t e;
   switch (mode) {
     case PW_F:

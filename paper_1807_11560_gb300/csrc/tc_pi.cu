@@ -377,15 +377,13 @@ cudaError_t launch_pi_tc(const Plan<float>& p, const PiEpi<float>& e, const floa
   cfg.blockDim = dim3(kThrP);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[2];
+  cudaLaunchAttribute at[3];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = (unsigned)e.nper;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
-  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = kUsePdl ? 2 : 1;
+  cfg.numAttrs = 1 + chain_attrs(at + 1);
   if ((err = cudaLaunchKernelEx(&cfg, kern, p, e, Lhat, P2, g, flag)) != cudaSuccess) return err;
   return cudaGetLastError();
 }

@@ -59,3 +59,24 @@ def test_binding_refuses_to_run_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(lddmm, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         lddmm.lib()
+
+
+def test_default_opts_fill_the_whole_struct_and_bad_options_are_refused(so):
+    """The binding's struct has the header's layout (the library's defaults land
+    in the right fields, up to the last one), and an out-of-range option is
+    refused before any CUDA call."""
+    import ctypes as ct
+    from paper_1807_11560_gb300 import lddmm
+    L = lddmm.lib()
+    o = lddmm.Opts()
+    ct.memset(ct.byref(o), 0x7f, ct.sizeof(o))
+    L.lddmm_default_opts(ct.byref(o))
+    assert (o.precision, o.use_graphs, o.persistent, o.tensor_cores) == (1, 1, 1, 1)
+    assert (o.recompute, o.autotune, o.newton, o.state_eq) == (0, 1, 0, 0)
+    assert o.debug_stall == 0
+    assert o.pcg_tol == 1e-12 and o.max_halvings == 10
+    h = ct.c_void_p()
+    arr = ct.c_int * 3
+    o.debug_stall = -1
+    assert L.lddmm_create(ct.byref(h), 3, arr(16, 16, 16), arr(8, 8, 8), 0.01, 2, 0.1, 4, ct.byref(o)) == 1
+    assert h.value is None
