@@ -132,7 +132,11 @@ k_iota_C(Plan<T> p, IotaDesc<T> d, const cplx<T>* __restrict__ T2) {
 
 // ---- pi C': real grid x1 -> half-spectrum h ----------------------------------------
 // CTA per (field, 256 consecutive positions): each thread streams its pencil
-// over x1 once (coalesced) and keeps the H1 complex sums in registers.
+// over x1 once (coalesced) and keeps the H1 complex sums in registers.  The
+// pencil is read kPiCBatch rows at a time, all loads of a batch issued before
+// its sums, so each thread keeps that many HBM reads in flight; the sums keep
+// their x1 order.
+constexpr int kPiCBatch = 8;
 template <typename T, int HR>
 __global__ void __launch_bounds__(kThreads)
 k_pi_C(Plan<T> p, PiSrc<T> s, cplx<T>* __restrict__ P2) {
@@ -151,15 +155,21 @@ k_pi_C(Plan<T> p, PiSrc<T> s, cplx<T>* __restrict__ P2) {
 #pragma unroll
   for (int h = 0; h < HR; ++h) acc[h] = C{T(0), T(0)};
   const T* __restrict__ src = s.src[f] + i;
-  for (int x = 0; x < G1; ++x) {
-    const T v = src[(long long)x * inner];
-    const C* e = sE + x * H1;
+  for (int x0 = 0; x0 < G1; x0 += kPiCBatch) {
+    T v[kPiCBatch];
 #pragma unroll
-    for (int h = 0; h < HR; ++h)
-      if (h < H1) {
-        acc[h].x = fma(v, e[h].x, acc[h].x);
-        acc[h].y = fma(v, e[h].y, acc[h].y);
-      }
+    for (int u = 0; u < kPiCBatch; ++u) v[u] = x0 + u < G1 ? src[(long long)(x0 + u) * inner] : T(0);
+#pragma unroll
+    for (int u = 0; u < kPiCBatch; ++u) {
+      if (x0 + u >= G1) break;
+      const C* e = sE + (x0 + u) * H1;
+#pragma unroll
+      for (int h = 0; h < HR; ++h)
+        if (h < H1) {
+          acc[h].x = fma(v[u], e[h].x, acc[h].x);
+          acc[h].y = fma(v[u], e[h].y, acc[h].y);
+        }
+    }
   }
   C* dst = P2 + (long long)f * H1 * inner + i;
 #pragma unroll
