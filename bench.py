@@ -299,8 +299,19 @@ FP32_LANES = 128
 # product, so its peak in algorithmic flops is a third of that
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
 # kernel classes whose contractions run on tcgen05 (3xTF32) in the per-evaluation
-# launches of padded grids above 32^3 points (the default tensor-core setting)
-TENSOR_CLASSES = ("iota_ab",)
+# launches of padded grids above 32^3 points (the default tensor-core setting):
+# iota A+B, C / bracket products / C', pi B'+A'
+TENSOR_CLASSES = ("iota_ab", "cpw", "pi_ba")
+
+
+def tensor_chain(args, Ks):
+    """True when the bracket evaluations run as per-evaluation tcgen05 kernels."""
+    import numpy as np
+    mvol = int(np.prod([(3 * k + 1) // 2 for k in Ks]))
+    persistent = args.persistent == "on" or (args.persistent == "auto" and mvol <= 32768)
+    if persistent or args.tensor_cores == "off":
+        return False
+    return args.tensor_cores == "on" or args.precision != "fp32" or mvol > 32768
 
 
 def pick_dominant(ctx, v, n_pcg):
@@ -451,7 +462,7 @@ def run_gpu(args):
             tensor = {"peak": tf32 / 3.0, "frac": achieved / (tf32 / 3.0),
                       "peak_source": f"{src} BF16 dense peak x 1.1/2.25 (nominal TF32/BF16) / 3 "
                                      f"(3xTF32: three TF32 MMAs per product; of {src})"}
-            if probe_cls in TENSOR_CLASSES:
+            if probe_cls in TENSOR_CLASSES and tensor_chain(args, Ks):
                 peak = tensor["peak"]
                 roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": tensor["peak_source"]}
             else:
