@@ -70,6 +70,25 @@ __device__ __forceinline__ void unflat(unsigned idx, unsigned n2, unsigned n3, i
   ix[0] = (int)q;
 }
 
+// This thread's voxel: with G3D the launch is a (32 x 8) block per 32 x3 by 8
+// x2 of one x1 plane (no index division; a warp covers 32 consecutive x3),
+// else one flat index per thread.  False for threads past the grid.
+template <bool G3D>
+__device__ __forceinline__ bool voxel(Dims g, unsigned& idx, int* ix) {
+  if (G3D) {
+    ix[2] = blockIdx.x * 32 + threadIdx.x;
+    ix[1] = blockIdx.y * 8 + threadIdx.y;
+    ix[0] = blockIdx.z;
+    if (ix[2] >= g.n3 || ix[1] >= g.n2) return false;
+    idx = ((unsigned)ix[0] * (unsigned)g.n2 + (unsigned)ix[1]) * (unsigned)g.n3 + (unsigned)ix[2];
+    return true;
+  }
+  idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.vol()) return false;
+  unflat(idx, g.n2, g.n3, ix);
+  return true;
+}
+
 // central difference d_j m at grid index ix (periodic), in unit-domain units
 template <typename T>
 __device__ __forceinline__ T cdiff(const T* __restrict__ m, const int* ix, int j, Dims g) {
@@ -82,15 +101,14 @@ __device__ __forceinline__ T cdiff(const T* __restrict__ m, const int* ix, int j
   return (mp - mq) * (T(0.5) * T(n[j]));
 }
 
-template <typename T>
+template <typename T, bool G3D>
 __global__ void __launch_bounds__(kThreads)
 k_transport(const T* __restrict__ m, const T* __restrict__ vn, const T* __restrict__ vc,
             T* __restrict__ mn, T* __restrict__ off, Dims g, T dt) {
   const long long vol = g.vol();
-  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= vol) return;
+  unsigned idx;
   int ix[3];
-  unflat(idx, g.n2, g.n3, ix);
+  if (!voxel<G3D>(g, idx, ix)) return;
   const int n[3] = {g.n1, g.n2, g.n3};
   T a[3], c0w[3];
   int c0[3], c1[3];
@@ -115,30 +133,28 @@ k_transport(const T* __restrict__ m, const T* __restrict__ vn, const T* __restri
   for (int j = 0; j < 3; ++j) off[j * vol + idx] = dsp[j];
 }
 
-template <typename T>
+template <typename T, bool G3D>
 __global__ void __launch_bounds__(kThreads)
 k_grad_dot(const T* __restrict__ m, const T* __restrict__ dv, T* __restrict__ s, Dims g) {
   const long long vol = g.vol();
-  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= vol) return;
+  unsigned idx;
   int ix[3];
-  unflat(idx, g.n2, g.n3, ix);
+  if (!voxel<G3D>(g, idx, ix)) return;
   T acc = T(0);
 #pragma unroll
   for (int j = 0; j < 3; ++j) acc = fma(cdiff(m, ix, j, g), dv[j * vol + idx], acc);
   s[idx] = acc;
 }
 
-template <typename T>
+template <typename T, bool G3D>
 __global__ void __launch_bounds__(kThreads)
 k_inc_step(const T* __restrict__ dm, const T* __restrict__ s, const T* __restrict__ mnext,
            const T* __restrict__ dvn, const T* __restrict__ off, T* __restrict__ dmn,
            T* __restrict__ sn, Dims g, T dt) {
   const long long vol = g.vol();
-  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= vol) return;
+  unsigned idx;
   int ix[3];
-  unflat(idx, g.n2, g.n3, ix);
+  if (!voxel<G3D>(g, idx, ix)) return;
   const int n[3] = {g.n1, g.n2, g.n3};
   T snew = T(0);
 #pragma unroll
@@ -580,22 +596,36 @@ __global__ void __launch_bounds__(kThreads) k_finalize_beta(const double* partia
 
 }  // namespace
 
+// planes of at least 32 x3 points take the (32 x 8)-block launch of voxel<true>
+inline bool plane_launch(Dims g) { return g.n3 >= 32; }
+inline dim3 plane_grid(Dims g) { return dim3((unsigned)(g.n3 + 31) / 32, (unsigned)(g.n2 + 7) / 8, (unsigned)g.n1); }
+
 template <typename T>
 void transport_step(const T* m, const T* vnext, const T* vcur, T* mnext, T* off, Dims g, double dt,
                     cudaStream_t st) {
-  k_transport<T><<<blocks_for(g.vol()), kThreads, 0, st>>>(m, vnext, vcur, mnext, off, g, (T)dt);
+  if (plane_launch(g))
+    k_transport<T, true><<<plane_grid(g), dim3(32, 8), 0, st>>>(m, vnext, vcur, mnext, off, g, (T)dt);
+  else
+    k_transport<T, false><<<blocks_for(g.vol()), kThreads, 0, st>>>(m, vnext, vcur, mnext, off, g, (T)dt);
 }
 
 template <typename T>
 void grad_dot(const T* m, const T* dv, T* s, Dims g, cudaStream_t st) {
-  k_grad_dot<T><<<blocks_for(g.vol()), kThreads, 0, st>>>(m, dv, s, g);
+  if (plane_launch(g))
+    k_grad_dot<T, true><<<plane_grid(g), dim3(32, 8), 0, st>>>(m, dv, s, g);
+  else
+    k_grad_dot<T, false><<<blocks_for(g.vol()), kThreads, 0, st>>>(m, dv, s, g);
 }
 
 template <typename T>
 void inc_step(const T* dm, const T* s, const T* mnext, const T* dvnext, const T* off, T* dmnext,
               T* snext, Dims g, double dt, cudaStream_t st) {
-  k_inc_step<T><<<blocks_for(g.vol()), kThreads, 0, st>>>(dm, s, mnext, dvnext, off, dmnext, snext, g,
-                                                         (T)dt);
+  if (plane_launch(g))
+    k_inc_step<T, true><<<plane_grid(g), dim3(32, 8), 0, st>>>(dm, s, mnext, dvnext, off, dmnext, snext, g,
+                                                               (T)dt);
+  else
+    k_inc_step<T, false><<<blocks_for(g.vol()), kThreads, 0, st>>>(dm, s, mnext, dvnext, off, dmnext, snext,
+                                                                   g, (T)dt);
 }
 
 template <typename T>
