@@ -859,9 +859,20 @@ struct Impl {
     ps.nf = 3;
     for (int c = 0; c < 3; ++c) ps.src[c] = prodM + (long long)c * Mvol;
     pb(PR_DEFORM);
-    iota_batch<T>(pad, d, Lhat, T2, st, nullptr);
-    def_products<T>(mode, fl, cached, prodM, Mvol, st);
-    pi_batch<T>(pad, ps, e, Lhat, T2, st);
+    if (use_tc_pad()) {
+      // with the per-evaluation tensor-core kernels: iota A+B and pi B'+A' as in
+      // the bracket evaluations, stages C and C' through the tcgen05 / SIMT
+      // transform kernels on the padded plan
+      bracket_iota<T>(pad, d, Lhat, T2, st, dres + 7);
+      iota_c_stage<T>(pad, d, T2, st, dres + 7);
+      def_products<T>(mode, fl, cached, prodM, Mvol, st);
+      pi_c_stage<T>(pad, ps, T2, st);
+      bracket_pi<T>(pad, e, Lhat, T2, st, dres + 7);
+    } else {
+      iota_batch<T>(pad, d, Lhat, T2, st, nullptr);
+      def_products<T>(mode, fl, cached, prodM, Mvol, st);
+      pi_batch<T>(pad, ps, e, Lhat, T2, st);
+    }
     pe(PR_DEFORM, grid_flops(M, d.nf + 3) + (mode == 1 ? 36.0 : 18.0) * (double)Mvol);
     launches += kIotaLaunches + 1 + kPiLaunches;
     check_launch("deformation product");

@@ -283,9 +283,7 @@ bool try_tc<float>(const Plan<float>& p, const IotaDesc<float>& d, const float2*
 }
 
 template <typename T>
-void iota_batch(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2, cudaStream_t st,
-                double* tc_flag) {
-  launch_iota_AB<T>(p, d, Lhat, T2, st);
+void iota_c_stage(const Plan<T>& p, const IotaDesc<T>& d, cplx<T>* T2, cudaStream_t st, double* tc_flag) {
   if (try_tc<T>(p, d, T2, tc_flag, st)) return;
   const long long nblk = ((long long)p.g.n2 * p.g.n3 + kThreads - 1) / kThreads;
   const size_t smem = (size_t)p.b.h1 * p.g.n1 * sizeof(cplx<T>);
@@ -296,14 +294,26 @@ void iota_batch(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* 
 }
 
 template <typename T>
-void pi_batch(const Plan<T>& p, const PiSrc<T>& s, const PiEpi<T>& e, const T* Lhat, cplx<T>* P2,
-              cudaStream_t st) {
+void iota_batch(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2, cudaStream_t st,
+                double* tc_flag) {
+  launch_iota_AB<T>(p, d, Lhat, T2, st);
+  iota_c_stage<T>(p, d, T2, st, tc_flag);
+}
+
+template <typename T>
+void pi_c_stage(const Plan<T>& p, const PiSrc<T>& s, cplx<T>* P2, cudaStream_t st) {
   const long long nblk = ((long long)p.g.n2 * p.g.n3 + kThreads - 1) / kThreads;
   const size_t smem = (size_t)p.b.h1 * p.g.n1 * sizeof(cplx<T>);
   const unsigned grid = (unsigned)(s.nf * nblk);
   if (p.b.h1 <= 8) launch_Cb<T, 8>(p, s, P2, grid, smem, st);
   else if (p.b.h1 <= 16) launch_Cb<T, 16>(p, s, P2, grid, smem, st);
   else launch_Cb<T, 32>(p, s, P2, grid, smem, st);
+}
+
+template <typename T>
+void pi_batch(const Plan<T>& p, const PiSrc<T>& s, const PiEpi<T>& e, const T* Lhat, cplx<T>* P2,
+              cudaStream_t st) {
+  pi_c_stage<T>(p, s, P2, st);
   launch_pi_BA<T>(p, e, Lhat, P2, st);
 }
 
@@ -391,6 +401,8 @@ void bracket_pi(const Plan<T>& p, const PiEpi<T>& e, const T* Lhat, const cplx<T
   template bool tile_valid<T>(const Plan<T>&, int, int, int);                                        \
   template void iota_batch<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t,    \
                               double*);                                                            \
+  template void iota_c_stage<T>(const Plan<T>&, const IotaDesc<T>&, cplx<T>*, cudaStream_t, double*); \
+  template void pi_c_stage<T>(const Plan<T>&, const PiSrc<T>&, cplx<T>*, cudaStream_t);             \
   template void pi_batch<T>(const Plan<T>&, const PiSrc<T>&, const PiEpi<T>&, const T*, cplx<T>*,  \
                             cudaStream_t);                                                         \
   template void bracket_iota<T>(const Plan<T>&, const IotaDesc<T>&, const T*, cplx<T>*, cudaStream_t, double*); \

@@ -142,6 +142,13 @@ struct PiEpi {
 template <typename T>
 void iota_batch(const Plan<T>& p, const IotaDesc<T>& d, const T* Lhat, cplx<T>* T2,
                 cudaStream_t st, double* tc_flag = nullptr);
+// stage C of iota alone (T2 from bracket_iota): the tcgen05 form where
+// tc_flag != nullptr and the plan supports it, else the SIMT kernel
+template <typename T>
+void iota_c_stage(const Plan<T>& p, const IotaDesc<T>& d, cplx<T>* T2, cudaStream_t st, double* tc_flag);
+// stage C' of pi alone: the C' sums of s into P2 [nf][h1][G2][G3] (for bracket_pi)
+template <typename T>
+void pi_c_stage(const Plan<T>& p, const PiSrc<T>& s, cplx<T>* P2, cudaStream_t st);
 // tcgen05 image-grid stage C (tc_iota.cu)
 bool iota_C_tc_supported(const Plan<float>& p);
 // tcgen05 iota stages A + B of a padded-grid bracket block (tc_bracket.cu)
