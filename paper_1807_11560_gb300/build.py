@@ -16,7 +16,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblddmm.so")
-SOURCES = ["dft.cu", "grid.cu", "sweep.cu", "tc_iota.cu", "tc_bracket.cu", "tc_pi.cu", "tc_cpw.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["dft.cu", "grid.cu", "sweep.cu", "tc_iota.cu", "tc_bracket.cu", "tc_pi.cu", "tc_cpw.cu",
+           "host_context.cu", "host_sweeps.cu", "host_deform.cu", "host_objective.cu", "host_solver.cu",
+           "host_components.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
