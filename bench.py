@@ -56,9 +56,10 @@ def parse():
                     help="image-grid band-to-grid transforms on tcgen05 (3xTF32): auto = grids >= 2^20 voxels")
     ap.add_argument("--persistent", default="auto", choices=["auto", "on", "off"],
                     help="band-limited sweeps as one persistent kernel: auto = padded grids up to 32^3")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "3xtf32", "bf16x3"],
+    ap.add_argument("--precision", default=None, choices=["fp32", "3xtf32", "bf16x3", "fp64"],
                     help="fp32: tensor cores per --tensor-cores (3xTF32); 3xtf32 / bf16x3: every contraction "
-                         "with a tensor-core kernel for its sizes on tcgen05 with that operand split")
+                         "with a tensor-core kernel for its sizes on tcgen05 with that operand split; fp64; "
+                         "default: the workload's (fp64 for 2d_64_blobs, else fp32)")
     ap.add_argument("--grid", default=None,
                     help="override the workload's image grid, e.g. 64,64,64 (a smaller case of the same "
                          "phantom and band, for kernel captures)")
@@ -67,6 +68,13 @@ def parse():
 
 
 SIZE_OVERRIDE = {}
+# GN iterations x PCG iterations of a workload's solve, and its default precision
+SOLVE_SHAPE = {"2d_64_blobs": (5, 10)}
+DEFAULT_PRECISION = {"2d_64_blobs": "fp64"}
+
+
+def solve_shape(name):
+    return SOLVE_SHAPE.get(name, (N_GN_CONFIG, N_PCG))
 
 
 def workload(name):
@@ -235,8 +243,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": name if not SIZE_OVERRIDE else f"{name} resized", "grid": list(Ns),
-                   "band": list(Ks), "Nt": Nt, "gn_iters": N_GN_CONFIG,
-                   "pcg_per_gn": N_PCG, "state": args.state, "l2": "oracle on host cores",
+                   "band": list(Ks), "Nt": Nt, "gn_iters": solve_shape(name)[0],
+                   "pcg_per_gn": solve_shape(name)[1], "state": args.state, "l2": "oracle on host cores",
                    "step": "one bounded sample: one GN Hessian-vector product at a fixed linearisation point"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample,
                          "host_cores": os.cpu_count(),
@@ -294,6 +302,7 @@ def measured_traffic(workload_name, cls):
 PROBE_CLASSES = ("sweep", "iota_ab", "cpw", "pi_ba", "inc_step", "transport", "iota_full", "pi_full", "deform")
 HBM_CLASSES = ("inc_step", "transport")
 FP32_LANES = 128
+NOMINAL_FP64_TFLOPS = 1.25
 # nominal dense tensor rates of the GB300 (PFLOP/s): TF32 takes the measured
 # BF16 peak times their ratio, and the 3xTF32 split issues three TF32 MMAs per
 # product, so its peak in algorithmic flops is a third of that
@@ -311,7 +320,9 @@ def tensor_chain(args, Ks):
     persistent = args.persistent == "on" or (args.persistent == "auto" and mvol <= 32768)
     if persistent or args.tensor_cores == "off":
         return False
-    return args.tensor_cores == "on" or args.precision != "fp32" or mvol > 32768
+    if args.precision == "fp64":
+        return False
+    return args.tensor_cores == "on" or args.precision in ("3xtf32", "bf16x3") or mvol > 32768
 
 
 def pick_dominant(ctx, v, n_pcg):
@@ -344,24 +355,29 @@ def run_gpu(args):
     name = args.workload
     kind, Ns, Ks, Nt, seed = workload(name)
     d = len(Ns)
+    n_gn, n_pcg = solve_shape(name)
+    fp64 = args.precision == "fp64"
+    RT = torch.float64 if fp64 else torch.float32
+    CT = torch.complex128 if fp64 else torch.complex64
     I0, I1 = inputs.make_pair(kind, Ns, rank_seed(seed, rank))
-    I0d = torch.as_tensor(I0, dtype=torch.float32, device=dev)
-    I1d = torch.as_tensor(I1, dtype=torch.float32, device=dev)
+    I0d = torch.as_tensor(I0, dtype=RT, device=dev)
+    I1d = torch.as_tensor(I1, dtype=RT, device=dev)
     ctx = Context(Ns, Ks, ALPHA, S, SIGMA, Nt, precision=args.precision,
                   tensor_cores={"auto": "auto", "on": True, "off": False}[args.tensor_cores], state=args.state,
                   persistent={"auto": "auto", "on": True, "off": False}[args.persistent])
     ctx.set_images(I0d, I1d)
-    v = torch.zeros((d,) + tuple(Ks), dtype=torch.complex64, device=dev)
+    v = torch.zeros((d,) + tuple(Ks), dtype=CT, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     class_ms = None
     probe_cls = args.probe
     if probe_cls == "auto":
-        probe_cls, class_ms = pick_dominant(ctx, v, N_PCG)
+        probe_cls, class_ms = pick_dominant(ctx, v, n_pcg)
 
-    # a step is one whole GN-Krylov solve from v0 = 0 (N_GN_CONFIG GN iterations
-    # x N_PCG PCG products), as a user runs it: its time is the GN solve time
+    # a step is one whole GN-Krylov solve from v0 = 0 (n_gn GN iterations
+    # x n_pcg PCG products, the workload's configuration), as a user runs it:
+    # its time is the GN solve time
     for _ in range(args.warmup):
-        ctx.gn_solve(v.clone(), N_GN_CONFIG, N_PCG)
+        ctx.gn_solve(v.clone(), n_gn, n_pcg)
 
     def barrier():
         if world > 1:
@@ -384,7 +400,7 @@ def run_gpu(args):
         flush.fill_(float(k))                             # L2 flush between steps (untimed)
         w = v.clone()
         starts[k].record()
-        rep_t = ctx.gn_solve(w, N_GN_CONFIG, N_PCG)
+        rep_t = ctx.gn_solve(w, n_gn, n_pcg)
         ends[k].record()
         hv += rep_t["pcg_iters"]
     barrier()
@@ -397,12 +413,12 @@ def run_gpu(args):
     # launch of the dominant kernel class (events perturb the step time, so
     # the headline value above is taken without them)
     ctx.probe(probe_cls)
-    ctx.gn_solve(v.clone(), 1, N_PCG)                     # builds the probed graph
+    ctx.gn_solve(v.clone(), 1, n_pcg)                     # builds the probed graph
     ctx.probe_read()
     barrier()
     for k in range(args.steps):
         flush.fill_(float(k))
-        ctx.gn_solve(v.clone(), N_GN_CONFIG, N_PCG)
+        ctx.gn_solve(v.clone(), n_gn, n_pcg)
     barrier()
     probe_ms, probe_n, probe_work = ctx.probe_read()
     ctx.probe(None)
@@ -413,7 +429,7 @@ def run_gpu(args):
     # pure Hessian-vector rate at a fixed linearisation point (context figure)
     g = torch.empty_like(v)
     ctx.gradient(v, g)
-    p = torch.as_tensor(inputs.random_bl(Ks, d, seed + 2, 1.0, Ns), dtype=torch.complex64, device=dev)
+    p = torch.as_tensor(inputs.random_bl(Ks, d, seed + 2, 1.0, Ns), dtype=CT, device=dev)
     out = torch.empty_like(p)
     for _ in range(3):
         ctx.hessvec(p, out)
@@ -429,16 +445,16 @@ def run_gpu(args):
 
 
     # end to end through the C interface with host buffers
-    I0h = torch.as_tensor(I0, dtype=torch.float32).pin_memory()
-    I1h = torch.as_tensor(I1, dtype=torch.float32).pin_memory()
-    vh = torch.zeros((d,) + tuple(Ks), dtype=torch.complex64).pin_memory()
+    I0h = torch.as_tensor(I0, dtype=RT).pin_memory()
+    I1h = torch.as_tensor(I1, dtype=RT).pin_memory()
+    vh = torch.zeros((d,) + tuple(Ks), dtype=CT).pin_memory()
     hv_e2e = 0
     barrier()
     te0 = time.perf_counter()
     for _ in range(args.steps):
         vh.zero_()
         ctx.set_images(I0h, I1h)
-        rep = ctx.gn_solve(vh, N_GN_CONFIG, N_PCG)
+        rep = ctx.gn_solve(vh, n_gn, n_pcg)
         hv_e2e += rep["pcg_iters"]
     barrier()
     te = time.perf_counter() - te0
@@ -466,11 +482,17 @@ def run_gpu(args):
                 peak = tensor["peak"]
                 roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": tensor["peak_source"]}
             else:
-                peak = sms * FP32_LANES * 2 * mhz * 1e6 / 1e12
-                roof = {"bound": "alu", "unit": "TFLOP/s",
-                        "peak_source": f"derived: {sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz "
-                                       "(median sampled SM clock); FP32 SIMT contraction",
-                        "vs_tensor_3xtf32": tensor}
+                if fp64:
+                    peak = NOMINAL_FP64_TFLOPS
+                    roof = {"bound": "alu", "unit": "TFLOP/s",
+                            "peak_source": f"nominal GB300 FP64 rate ({NOMINAL_FP64_TFLOPS} TFLOP/s); FP64 SIMT "
+                                           "contraction"}
+                else:
+                    peak = sms * FP32_LANES * 2 * mhz * 1e6 / 1e12
+                    roof = {"bound": "alu", "unit": "TFLOP/s",
+                            "peak_source": f"derived: {sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz "
+                                           "(median sampled SM clock); FP32 SIMT contraction",
+                            "vs_tensor_3xtf32": tensor}
             wunit = "flop"
         roof.update({"kernel": probe_cls, "achieved": achieved, "peak": peak, "frac": achieved / peak,
                      "traffic": measured_traffic(name, probe_cls), "traffic_unit": "B per launch (ncu)",
@@ -496,12 +518,12 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
             "config": {"workload": name if not SIZE_OVERRIDE else f"{name} resized", "grid": list(Ns),
                        "band": list(Ks), "Nt": Nt,
-                       "gn_iters": N_GN_CONFIG, "pcg_per_gn": N_PCG, "state": args.state,
-                       "step": f"one GN-Krylov solve from v0 = 0: {N_GN_CONFIG} GN iterations (gradient, "
-                               f"{N_PCG} PCG Hessvecs, Armijo)",
+                       "gn_iters": n_gn, "pcg_per_gn": n_pcg, "state": args.state,
+                       "step": f"one GN-Krylov solve from v0 = 0: {n_gn} GN iterations (gradient, "
+                               f"{n_pcg} PCG Hessvecs, Armijo)",
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{world}",
                        "precision": args.precision,
@@ -658,6 +680,8 @@ def run_band_sweep(args):
 
 def main():
     args = parse()
+    if args.precision is None:
+        args.precision = DEFAULT_PRECISION.get(args.workload, "fp32")
     if args.grid:
         SIZE_OVERRIDE["grid"] = tuple(int(x) for x in args.grid.split(","))
     if args.band:

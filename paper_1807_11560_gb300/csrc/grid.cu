@@ -101,8 +101,10 @@ __device__ __forceinline__ T cdiff(const T* __restrict__ m, const int* ix, int j
   return (mp - mq) * (T(0.5) * T(n[j]));
 }
 
+// (FP32 plane launches: 32 registers, so eight blocks per SM keep more of the
+// 32 corner gathers of a voxel in flight)
 template <typename T, bool G3D>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && G3D) ? 8 : 0)
 k_transport(const T* __restrict__ m, const T* __restrict__ vn, const T* __restrict__ vc,
             T* __restrict__ mn, T* __restrict__ off, Dims g, T dt) {
   const long long vol = g.vol();
