@@ -20,10 +20,8 @@
 // every x2 a warp stores 32 consecutive x3 of T2 (256 contiguous bytes).
 // Global loads are batched (eight per thread in flight); the twiddle operands
 // are expanded once per context and copied into each CTA; the common padded
-// sizes are compile-time constants.  A work item is about 96 rows of band
-// slabs (3 slabs at K2 = 32), so a bracket block's 24 x K1/2 slabs make at
-// most one item per SM (one CTA of 512 threads per SM, up to 512 TMEM columns;
-// smaller plans keep two CTAs per SM); every MMA wait is bounded.
+// sizes are compile-time constants.  One CTA of 512 threads per SM (512 TMEM
+// columns); every MMA wait is bounded.
 #include <algorithm>
 #include <cstdint>
 
@@ -323,16 +321,15 @@ bool ab_tc_geom(const Plan<float>& p, AbTc& g, size_t& smem) {
   g.NA = r16(2 * G3);
   g.NB = r16(2 * G2);
   if (g.NA > 256 || g.NB > 256) return false;
-  // about 96 rows of band slabs per item: at most one item per SM for the 24
-  // fields of a bracket block (no SM runs two items while others idle), and
-  // a short chain per item
-  g.S = std::max(1, std::min(kMTile / K2, 96 / K2));
+  // about 64 rows of band slabs per item: enough items for every SM, and a
+  // short chain per item
+  g.S = std::max(1, std::min(kMTile / K2, 64 / K2));
   g.passes = (g.S * G3 + kMTile - 1) / kMTile;
   // stage B reuses stage A's columns when a single pass reads stage A's
   // result once
   g.colB = g.passes == 1 ? 0 : g.NA;
   g.tcols = pow2t(std::max(g.NA, g.colB + g.passes * g.NB));
-  if (g.tcols > 512) return false;
+  if (g.tcols > 256) return false;                  // two items per SM
   const int Kmax = std::max(g.KA, g.KB);
   g.rows = (std::max(g.S * K2, std::min(g.S * G3, kMTile)) + 7) / 8 * 8;
   g.tw = 2 * std::max(g.NA * g.KA, g.NB * g.KB);
@@ -340,7 +337,7 @@ bool ab_tc_geom(const Plan<float>& p, AbTc& g, size_t& smem) {
   // the 128-row reads of the lo half stay inside the allocation
   floats = std::max(floats, (size_t)g.rows * Kmax + (size_t)kMTile * Kmax);
   smem = floats * sizeof(float) + 16;
-  return smem <= (g.tcols > 256 ? 200 : 112) * 1024;   // one or two items per SM
+  return smem <= 112 * 1024;
 }
 
 }  // namespace
@@ -377,7 +374,7 @@ cudaError_t launch_ab_tc(const Plan<float>& p, const IotaDesc<float>& d, const f
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const int nitems = (d.nf * p.b.h1 + g.S - 1) / g.S;
-  const unsigned grid = (unsigned)std::min(nitems, (g.tcols > 256 ? 1 : 2) * sms);
+  const unsigned grid = (unsigned)std::min(nitems, 2 * sms);
   // programmatic stream serialisation: the prologue (twiddle copy, TMEM
   // allocation) overlaps the tail of the previous kernel
   cudaLaunchConfig_t cfg = {};
