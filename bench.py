@@ -166,60 +166,103 @@ class Clocks:
 ORACLE_MAX_WORKERS = 16
 
 
-def _oracle_problem(name, state):
+def _oracle_problem(spec, state, quant):
+    """The oracle problem of a workload (kind, grid, band, Nt, seed), with the
+    seeded v0 and direction p; quant: the inputs rounded to FP32 first, as the
+    FP32 library receives them."""
+    import numpy as np
     from oracle import deformation, objective
     from paper_1807_11560_gb300 import inputs
-    kind, Ns, Ks, Nt, seed = workload(name)
+    kind, Ns, Ks, Nt, seed = spec
     I0, I1 = inputs.make_pair(kind, Ns, seed)
-    cls = deformation.DeformationProblem if state == "deformation" else objective.Problem
-    P = cls(I0, I1, Ks, ALPHA, S, SIGMA, Nt)
     v0 = inputs.random_bl(Ks, len(Ns), seed + 1, 2.0, Ns)
     p = inputs.random_bl(Ks, len(Ns), seed + 2, 1.0, Ns)
+    if quant:
+        I0, I1 = (np.asarray(x, np.float32).astype(np.float64) for x in (I0, I1))
+        v0, p = (np.asarray(x, np.complex64).astype(np.complex128) for x in (v0, p))
+    cls = deformation.DeformationProblem if state == "deformation" else objective.Problem
+    P = cls(I0, I1, Ks, ALPHA, S, SIGMA, Nt)
     return P, v0, p
 
 
-def _oracle_worker(name, state, jobs, barrier, results):
+def _oracle_worker(spec, state, quant, keep, jobs, barrier, results):
     """Linearise once (untimed, the worker's warm-up), wait for every worker,
-    then take Hessian-vector products from the shared job counter."""
-    P, v0, p = _oracle_problem(name, state)
+    then take Hessian-vector products from the shared job counter; with keep,
+    also return (E, g, H p) of the last product."""
+    P, v0, p = _oracle_problem(spec, state, quant)
     lin = P.gradient(v0)
     barrier.wait()
     times = []
+    Hp = None
     while True:
         with jobs.get_lock():
             if jobs.value <= 0:
                 break
             jobs.value -= 1
         t0 = time.perf_counter()
-        P.hessvec(lin, p)
+        Hp = P.hessvec(lin, p)
         times.append(time.perf_counter() - t0)
-    results.put(times)
+    results.put((times, (lin.E, lin.g, Hp) if keep and Hp is not None else None))
 
 
-def oracle_hessvec_rate(name, n_hv, state="image", workers=1):
+def oracle_hessvec_rate(name, n_hv, state="image", workers=1, keep=False, quant=False):
     """FP64 oracle Hessian-vector products at a fixed linearisation point:
     n_hv products shared by `workers` processes.  Returns (products per second
-    of wall time, per-product times, wall seconds)."""
+    of wall time, per-product times, wall seconds, (E, g, H p) of one product
+    when keep, else None)."""
     import multiprocessing as mp
     for var in ("OMP_NUM_THREADS", "MKL_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
         os.environ[var] = "1"
+    spec = workload(name)
     ctx = mp.get_context("spawn")
     barrier = ctx.Barrier(workers + 1)
     jobs = ctx.Value("i", n_hv)
     results = ctx.Queue()
-    procs = [ctx.Process(target=_oracle_worker, args=(name, state, jobs, barrier, results))
+    procs = [ctx.Process(target=_oracle_worker, args=(spec, state, quant, keep, jobs, barrier, results))
              for _ in range(workers)]
     for q in procs:
         q.start()
     barrier.wait()
     t0 = time.perf_counter()
-    times = []
+    times, ref = [], None
     for _ in procs:
-        times += results.get()
+        t, r = results.get()
+        times += t
+        ref = ref if ref is not None else r
     wall = time.perf_counter() - t0
     for q in procs:
         q.join()
-    return len(times) / wall, times, wall
+    return len(times) / wall, times, wall, ref
+
+
+def oracle_parity(ctx, ref, Ns, Ks, seed, CT):
+    """Energy, gradient and GN Hessian-vector product of the library at the
+    oracle's seeded point (v0, p) against the oracle's (E, g, H p) from the CPU
+    leg: relative errors, each the larger of the l2 and the element-wise
+    (max |a - b| / max |b|) measure."""
+    import numpy as np
+    import torch
+
+    from paper_1807_11560_gb300 import inputs
+    if ref is None:
+        return None
+    E_ref, g_ref, H_ref = ref
+    d = len(Ns)
+    v0 = torch.as_tensor(inputs.random_bl(Ks, d, seed + 1, 2.0, Ns), dtype=CT, device="cuda")
+    pv = torch.as_tensor(inputs.random_bl(Ks, d, seed + 2, 1.0, Ns), dtype=CT, device="cuda")
+    g = torch.empty_like(v0)
+    E = ctx.gradient(v0, g)
+    Hp = torch.empty_like(v0)
+    ctx.hessvec(pv, Hp)
+
+    def rel(a, b):
+        a = a.detach().cpu().numpy().astype(np.complex128)
+        return float(max(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()),
+                         np.abs(a - b).max() / np.abs(b).max()))
+    return {"energy_rel_err": abs(E - E_ref) / abs(E_ref), "gradient_rel_err": rel(g, g_ref),
+            "hessvec_rel_err": rel(Hp, H_ref), "target": 1e-5,
+            "point": "the oracle CPU leg's seeded v0 and direction p (inputs rounded to the "
+                     "library's precision), one gradient and one GN product"}
 
 
 def oracle_workers(n):
@@ -233,7 +276,7 @@ def run_reference(args):
     name = args.workload
     kind, Ns, Ks, Nt, seed = workload(name)
     workers = oracle_workers(args.steps)
-    value, times, wall = oracle_hessvec_rate(name, args.steps, state=args.state, workers=workers)
+    value, times, wall, _ = oracle_hessvec_rate(name, args.steps, state=args.state, workers=workers)
     sample = (f"{len(times)} GN Hessian-vector products of the FP64 NumPy oracle at a fixed "
               f"linearisation point ({name}), one per step, spread over {workers} worker processes "
               "(one host core each; each worker's untimed linearisation is its warm-up)")
@@ -503,10 +546,13 @@ def run_gpu(args):
         if class_ms:
             roof["class_ms_one_gn_iteration"] = class_ms
         cpu = None
+        parity = None
         if not args.no_cpu_baseline:
-            one, t1, _ = oracle_hessvec_rate(name, 1, state=args.state, workers=1)
+            one, t1, _, ref = oracle_hessvec_rate(name, 1, state=args.state, workers=1, keep=True,
+                                                  quant=not fp64)
             nw = oracle_workers(os.cpu_count() or 1)
-            allc, tall, _ = oracle_hessvec_rate(name, nw, state=args.state, workers=nw)
+            allc, tall, _, _ = oracle_hessvec_rate(name, nw, state=args.state, workers=nw)
+            parity = oracle_parity(ctx, ref, Ns, Ks, seed, CT)
             cpu = {"value": allc, "unit": UNIT, "cores": nw, "kind": "oracle",
                    "sample": f"{nw} GN Hessian-vector products of the FP64 NumPy oracle on {name} at a "
                              f"fixed linearisation point, one per worker process on {nw} host cores "
@@ -538,6 +584,7 @@ def run_gpu(args):
             "wall_s": t_wall,
             "roofline": roof,
             "cpu_baseline": cpu,
+            "oracle_parity": parity,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 2 * nvox * 4 + nband * 8, "d2h_bytes_per_step": nband * 8},
             "gpu_launches": launches,
