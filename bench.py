@@ -642,12 +642,37 @@ def run_population(args):
             hv += sum(r["pcg_iters"] for r in reps)
         return hv / t, t / steps, v0s
 
+    # one pair of each grid and band: gradient and GN product at the pair's seeded
+    # point, for the split-precision against the plain FP32 comparison
+    picked, seen = [], set()
+    for i, (_, Ns, Ks, _, _) in enumerate(pop):
+        if (tuple(Ns), tuple(Ks)) not in seen:
+            seen.add((tuple(Ns), tuple(Ks)))
+            picked.append(i)
+
+    def products(made):
+        out = {}
+        for i in picked:
+            _, Ns, Ks, _, seed = pop[i]
+            v0 = inputs.random_bl(Ks, 3, seed + 1, 2.0, Ns).astype(np.complex64)
+            pv = inputs.random_bl(Ks, 3, seed + 2, 1.0, Ns).astype(np.complex64)
+            g, Hp = np.empty_like(v0), np.empty_like(v0)
+            made[i][0].gradient(v0, g)
+            made[i][0].hessvec(pv, Hp)
+            out[i] = (g.astype(np.complex128), Hp.astype(np.complex128))
+        return out
+
+    def rel(a, b):
+        return float(max(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()),
+                         np.abs(a - b).max() / np.abs(b).max()))
+
     made = make("auto")
     timed(made, args.warmup, 0)
     clocks = Clocks()
     value, step_s, v_tc = timed(made, args.steps, 0)
     clk = clocks.stop()
     seq_value, _, _ = timed(made, 1, 1)
+    prod_tc = products(made)
     held = sum(m[0].device_bytes for m in made)
     for m in made:
         m[0].close()
@@ -655,6 +680,7 @@ def run_population(args):
     made = make(False)
     timed(made, 1, 0)
     plain_value, _, v_plain = timed(made, args.steps, 0)
+    prod_plain = products(made)
     for m in made:
         m[0].close()
     # one GN step from v0 = 0 on the same images: the two precisions' updates
@@ -671,6 +697,10 @@ def run_population(args):
         "sequential_value": seq_value,
         "plain_fp32_value": plain_value,
         "split_vs_plain_rel_update_diff_max": max(diffs),
+        "split_vs_plain_product_rel_diff_max": {
+            "gradient": max(rel(prod_tc[i][0], prod_plain[i][0]) for i in picked),
+            "hessvec": max(rel(prod_tc[i][1], prod_plain[i][1]) for i in picked),
+            "pairs": len(picked), "measure": "larger of l2 and element-wise, one pair per grid and band"},
         "device_bytes_held": held,
         "clocks": clk,
     }
